@@ -1,0 +1,48 @@
+"""Dense gradients of ``loss(theta, b) = ||x - x_t||^2`` with ``A(theta) x = b``
+on tiny grids (plain linear algebra on the dense operator; no TT solver).
+
+With ``A(theta) = sum_k theta_k (I x .. x L x .. x I)`` (L in position k):
+
+* ``lambda = A^{-T} 2 (x - x_t)`` (adjoint solve),
+* ``d loss / d b = lambda``,
+* ``d loss / d theta_k = - lambda^T (I x .. x L x .. x I) x``,
+* ``d loss / d C_k[a, i, c] = sum_{alpha, beta} lambda[alpha, i, beta]
+  P_{<k}[alpha, a] Q_{>k}[beta, c]`` where ``P_{<k}`` and ``Q_{>k}`` are the
+  left and right interface matrices of b's TT (Section 2.2).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import tt as ttm
+from . import closed_forms as cf
+
+
+def loss_and_grads(theta, L, b_cores, xt_cores):
+    """Loss and gradients w.r.t. ``theta`` and b's cores (dense)."""
+    d = len(b_cores)
+    ns = [c.shape[1] for c in b_cores]
+    mats = [t * L for t in theta]
+    bfull = ttm.full(b_cores)
+    x = cf.kron_sum_solve_dense(mats, bfull)
+    xt = ttm.full(xt_cores)
+    g = 2.0 * (x - xt)
+    lam = cf.kron_sum_solve_dense([M.T for M in mats], g)
+    loss = float(np.sum((x - xt) ** 2))
+    X = x.reshape(ns)
+    dtheta = np.zeros(d)
+    for k in range(d):
+        LX = np.moveaxis(np.tensordot(L, X, axes=([1], [k])), 0, k).reshape(-1)
+        dtheta[k] = -float(lam @ LX)
+    dcores = []
+    for k in range(d):
+        left = np.ones((1, 1))
+        for c in b_cores[:k]:
+            left = (left @ c.reshape(c.shape[0], -1)).reshape(-1, c.shape[2])
+        right = np.ones((1, 1))
+        for c in reversed(b_cores[k + 1:]):
+            right = (c.reshape(-1, c.shape[2]) @ right.T).reshape(c.shape[0], -1).T
+        # left: (n_<k, r_{k-1}); right: (n_>k, r_k)
+        Lam = lam.reshape(left.shape[0], ns[k], right.shape[0])
+        dcores.append(np.einsum("xiy,xa,yc->aic", Lam, left, right))
+    return loss, dtheta, dcores, x, lam
