@@ -1,0 +1,244 @@
+/*
+ * ttsg.h - C ABI of the GB300 randomized sketched TT-GMRES library.
+ *
+ * Solves A x = b where A is a tensor-train (TT) operator and x, b are TT
+ * vectors, with the sketched TT-GMRES of Bucci, Palitta and Robol,
+ * "Randomized sketched TT-GMRES for linear systems with tensor structure"
+ * (arXiv 2409.09471), Algorithm 4 with incomplete orthogonalisation l = 1.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Layout.  All arrays are row-major (C order).
+ *   TT vector core k  : [r_{k-1}][n_k][r_k], r_0 = r_d = 1           (Sec. 2.2, eq. tt-format)
+ *   TT operator core k: [R_{k-1}][n_k (out)][n_k (in)][R_k], R_0=R_d=1 (Sec. 2.2, eq. operator tt-format)
+ *   Khatri-Rao factor k: [s][n_k]                                       (Sec. 3.1)
+ *   The merged rank index of a matvec output is a * r + l (operator rank a
+ *   slowest), so output core k has ranks R_{k-1} r_{k-1} and R_k r_k.
+ * Memory.  Core pointers, factor pointers, workspaces and outputs marked
+ *   "device" are CUDA device pointers on the current device; arrays of
+ *   pointers and of sizes (n, rank, ...) are HOST arrays.  The caller owns all
+ *   memory; the library allocates nothing except where stated.
+ * Precision.  ``mode`` selects the arithmetic:
+ *   TT_MODE_FP64  cores are double; every step in FP64.
+ *   TT_MODE_FP32  cores are float; contractions in FP32 (CUDA cores),
+ *                 Householder QR, least squares and residual checks in FP64.
+ *   TT_MODE_TF32  cores are float; contractions on tcgen05 tensor cores in TF32
+ *                 with FP32 accumulation; QR, least squares, residual in FP64.
+ * Streams.  ``stream`` is a cudaStream_t (NULL = default stream).  Calls that
+ *   return host values or data-dependent ranks synchronise that stream.
+ * Workspace.  Entry points that need scratch take ``ws`` (device) and
+ *   ``ws_bytes``; the matching *_workspace function returns the bytes needed.
+ *   A workspace may be reused by consecutive calls on the same stream.
+ * Errors.  Every function returns TT_OK (0) or a TT_ERR_* code; tt_last_error()
+ *   returns a message for the calling thread's last failure.  Argument errors
+ *   are detected on the host before any launch.
+ */
+#ifndef TTSG_H
+#define TTSG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define TT_OK 0
+#define TT_ERR_ARG 1           /* bad shape, rank, pointer or parameter */
+#define TT_ERR_WORKSPACE 2     /* ws_bytes smaller than the *_workspace answer */
+#define TT_ERR_CUDA 3          /* a CUDA runtime call or kernel failed */
+#define TT_ERR_TIMEOUT 4       /* a bounded device-side wait expired */
+#define TT_ERR_NOT_CONVERGED 5 /* solver stopped at maxit / restarts; x is returned */
+#define TT_ERR_UNSUPPORTED 6   /* mode or size not supported by this build */
+
+#define TT_MODE_FP64 0
+#define TT_MODE_FP32 1
+#define TT_MODE_TF32 2
+
+#define TT_MAX_D 64
+
+/* TT vector (input).  n[d], rank[d+1]: host arrays; core[d]: host array of
+ * device pointers. */
+typedef struct {
+  int d;
+  const int64_t* n;
+  const int64_t* rank;
+  void* const* core;
+} tt_vec;
+
+/* TT vector (output with data-dependent ranks).  core[k] must hold at least
+ * cap[k] * n[k] * cap[k+1] elements; the result is written compactly as
+ * [rank[k]][n[k]][rank[k+1]] and rank[] (host, d+1 entries) is filled in. */
+typedef struct {
+  int d;
+  const int64_t* n;
+  const int64_t* cap;
+  int64_t* rank;
+  void* const* core;
+} tt_vec_out;
+
+/* TT operator (square modes).  n[d], rank[d+1]: host; core[d]: device. */
+typedef struct {
+  int d;
+  const int64_t* n;
+  const int64_t* rank;
+  void* const* core;
+} tt_op;
+
+/* Library version string. */
+const char* tt_version(void);
+/* Message of the calling thread's last error ("" if none). */
+const char* tt_last_error(void);
+
+/*
+ * tt_matvec - y = A x without truncation (Sec. 2.2, matvec formula):
+ *   G_k[(a,l), i, (a',l')] = sum_j D_k[a, i, j, a'] C_k[l, j, l'].
+ * y->core[k] (device) must hold (R_{k-1} r_{k-1}) * n_k * (R_k r_k) elements;
+ * y's ranks are R_k r_k exactly and y->n/rank must say so (checked).
+ * Operator and vector cores use the precision of ``mode``.
+ */
+int tt_matvec(int mode, const tt_op* A, const tt_vec* x, const tt_vec* y,
+              void* ws, size_t ws_bytes, void* stream);
+size_t tt_matvec_workspace(int mode, const tt_op* A, const tt_vec* x);
+
+/*
+ * tt_sketch - Khatri-Rao sketch of a TT vector (Sec. 3.1):
+ *   out[j] = prod_k ( sum_i S_k[j, i] C_k[:, i, :] ),  j = 0..s-1,
+ * computed as one left-to-right sweep over the cores for all s rows.
+ * S[k] (device): factor k, [s][n_k], same precision as the cores.
+ * out (device, double[s]).
+ */
+int tt_sketch(int mode, const tt_vec* x, int64_t s, void* const* S, double* out,
+              void* ws, size_t ws_bytes, void* stream);
+size_t tt_sketch_workspace(int mode, const tt_vec* x, int64_t s);
+
+/*
+ * tt_dot - <x, y> by the left-to-right Gram sweep (used for h_{k,k} = w^T v_k
+ * and the norms of Alg. 4).  out (device, double[1]).
+ */
+int tt_dot(int mode, const tt_vec* x, const tt_vec* y, double* out,
+           void* ws, size_t ws_bytes, void* stream);
+size_t tt_dot_workspace(int mode, const tt_vec* x, const tt_vec* y);
+
+/*
+ * tt_round_rand - randomize-then-orthogonalize rounding (Sec. 3.3) of the
+ * implicit sum  sum_b coef[b] * X_b  (nterms >= 1 TT vectors with equal mode
+ * sizes), without forming the block cores:
+ *   1. sketch ranks l_mu = min(rmax + oversample, t_mu, l_{mu-1} n_mu,
+ *      prod_{k>mu} n_k) with t_mu the summed representation ranks;
+ *   2. right partial contractions of every term with a Gaussian TT-DRM;
+ *   3. left-to-right sweep: Y = Z W, FP64 Householder QR of Y, core <- Q,
+ *      M = Q^T Z carried into the next core;
+ *   4. right-to-left truncation: FP64 Householder QR of the core unfolding and
+ *      a small Jacobi SVD; per-bond threshold eps ||T|| / sqrt(d-1), ranks
+ *      capped at rmax.  Cores 2..d of the result are right-orthogonal.
+ * coef: host array [nterms].  drm: NULL to draw the TT-DRM from the Philox
+ * stream (seed, streams 2048 + k) with capacity ranks rmax + oversample, or a
+ * host array of d device pointers to DRM cores [L_{k-1}][n_k][L_k] with ranks
+ * drm_rank[d+1] (host) at least the sketch ranks (leading sub-blocks are used).
+ * y: output with capacities; ranks written to y->rank.  Synchronises.
+ */
+int tt_round_rand(int mode, int nterms, const tt_vec* terms, const double* coef,
+                  double eps, int64_t rmax, int64_t oversample, uint64_t seed,
+                  void* const* drm, const int64_t* drm_rank, const tt_vec_out* y,
+                  void* ws, size_t ws_bytes, void* stream);
+size_t tt_round_rand_workspace(int mode, int nterms, const tt_vec* terms, int64_t rmax,
+                               int64_t oversample);
+
+/*
+ * tt_gaussian - fill out (device, ``count`` elements: double for TT_MODE_FP64,
+ * float otherwise) with std times element e of the Gaussian stream (seed,
+ * stream_id): Philox4x32-10 (Salmon et al., SC'11) with counter (lo(e/2),
+ * hi(e/2), lo(stream_id), hi(stream_id)) and key (lo(seed), hi(seed)); the
+ * output words w0..w3 give u1 = ((w0<<32|w1)>>11 + 0.5) 2^-53 and u2 likewise
+ * from (w2, w3); element e is sqrt(-2 ln u1) cos(2 pi u2) for even e and
+ * sqrt(-2 ln u1) sin(2 pi u2) for odd e.  The solver draws Khatri-Rao factor k
+ * from stream 1024 + k and TT-DRM core k from stream 2048 + k.
+ */
+int tt_gaussian(int mode, void* out, int64_t count, uint64_t seed, uint64_t stream_id,
+                double std_, void* stream);
+
+/*
+ * tt_qr_f64 - FP64 Householder QR of a tall matrix Y (m x l, m >= l) read
+ * with strides (row stride sr, column stride sc) in the mode's type.  Writes
+ * the explicit Q (m x l, row-major, mode's type) if Q != NULL and R (l x l,
+ * row-major, double) if R != NULL.  Used inside tt_round_rand; exposed for
+ * testing.  All pointers device.
+ */
+int tt_qr_f64(int mode, const void* Y, int64_t m, int64_t l, int64_t sr, int64_t sc,
+              void* Q, double* R, void* ws, size_t ws_bytes, void* stream);
+size_t tt_qr_f64_workspace(int64_t m, int64_t l);
+
+/*
+ * tt_lstsq_f64 - sketched least squares of eq. pseudo_inv:
+ *   y = argmin ||W y - c||_2 with W (s x k, column-major, device double) and
+ * c (device double[s]); writes y (device double[k]) and res = ||W y - c||
+ * (device double[1]).  Householder QR in FP64 on the device.
+ */
+int tt_lstsq_f64(const double* W, int64_t s, int64_t k, const double* c, double* y,
+                 double* res, void* ws, size_t ws_bytes, void* stream);
+size_t tt_lstsq_f64_workspace(int64_t s, int64_t k);
+
+/* Solver parameters (Alg. 4 inputs plus the restart loop of Sec. 3.4). */
+typedef struct {
+  int maxit;          /* Krylov dimension cap per cycle (maxit) */
+  int s;              /* sketch rows; 0 => 2 * maxit (Sec. 3.6) */
+  double tol;         /* target true relative residual ||b - A x|| / ||b|| */
+  double round_tol;   /* Gram-Schmidt rounding tolerance; 0 => eta * tol */
+  double eta;         /* rounding threshold factor (Alg. 4 input eta) */
+  double stop_safety; /* sketched stop at stop_safety * tol (relative) */
+  int64_t rmax;       /* rank cap of the basis vectors (Sec. 4.2) */
+  int64_t r_sol;      /* rank cap of the solution; 0 => rmax */
+  int64_t oversample; /* randomized-rounding oversampling p */
+  uint64_t seed;      /* Khatri-Rao factors: stream 1024+k; TT-DRM: 2048+k */
+  int max_restarts;   /* restart cycles after the first */
+  int mode;           /* TT_MODE_* */
+} tt_solver_params;
+
+typedef struct {
+  int iters;            /* total Krylov iterations over all cycles */
+  int cycles;           /* restart cycles run */
+  double sketched_res;  /* last sketched relative residual */
+  double true_res;      /* final true relative residual (FP64, exact TT) */
+  int64_t max_rank;     /* largest basis rank seen */
+  int status;           /* TT_OK or TT_ERR_NOT_CONVERGED */
+  double seconds;       /* host wall time of the call */
+  double* res_hist;     /* optional host array [hist_cap]: sketched residuals */
+  int64_t* rank_hist;   /* optional host array [hist_cap]: basis max ranks */
+  int hist_cap;
+  int svd_nonconverged; /* small SVDs that reached their sweep cap (diagnostic) */
+} tt_solver_info;
+
+/*
+ * tt_sgmres_solve - restarted TT-sGMRES (Alg. 4, l = 1, randomized rounding),
+ * x0 = 0.  Each cycle stops when ||W y - S r0|| <= stop_safety * tol * ||b|| /
+ * ||r|| * ||S r0||; the final x of a cycle is one randomized rounding of
+ * sum_i y_i v_i (Sec. 3.5); the true residual is then computed exactly in FP64
+ * and the loop restarts from it until ||b - A x|| <= tol ||b||.
+ * A and b are given in FP64 (double cores, device); x (device, double cores,
+ * capacities >= r_sol) receives the solution.  Synchronises.
+ */
+int tt_sgmres_solve(const tt_op* A, const tt_vec* b, const tt_solver_params* p,
+                    const tt_vec_out* x, tt_solver_info* info, void* ws, size_t ws_bytes,
+                    void* stream);
+size_t tt_sgmres_solve_workspace(const tt_op* A, const tt_vec* b, const tt_solver_params* p);
+
+/*
+ * Measurement support (no counterpart in the method): tt_profile(mask) clears
+ * the launch records and, for every class bit set in mask (1 GEMM, 2 FP64 QR,
+ * 4 Jacobi SVD, 8 least squares, 16 copies / generators), brackets each later
+ * launch of that class with CUDA events on its stream.  tt_profile_read
+ * synchronises those events and returns, for one class index (0..4), the summed
+ * event time in milliseconds, the number of launches and their algorithmic
+ * FLOPs and bytes (host outputs, any may be NULL).  tt_profile(0) disables it.
+ */
+int tt_profile(int mask);
+int tt_profile_read(int cls, double* ms_total, int64_t* launches, double* flops, double* bytes);
+/* Number of kernel launches this library has enqueued since it was loaded
+ * (all classes, counted on the host whether or not profiling is enabled). */
+int64_t tt_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TTSG_H */

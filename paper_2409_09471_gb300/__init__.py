@@ -1,0 +1,274 @@
+"""Python binding of the GB300 randomized sketched TT-GMRES library (libttsg.so).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+library behind the C ABI declared in ``include/ttsg.h``.  PyTorch provides
+device memory and the current CUDA stream.  The functions keep the C names:
+
+``tt_matvec``, ``tt_sketch``, ``tt_dot``, ``tt_round_rand``, ``tt_gaussian``,
+``tt_qr_f64``, ``tt_lstsq_f64``, ``tt_sgmres_solve``.
+
+TT vectors are :class:`TT` objects (a list of contiguous CUDA tensors with
+shapes ``[r_{k-1}, n_k, r_k]``); TT operators are lists of contiguous CUDA
+tensors ``[R_{k-1}, n, n, R_k]``.  Importing this module fails loudly when the
+compiled library is missing; there is no fallback implementation.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import List, Sequence
+
+import torch
+
+from ._abi import (lib, TTVec, TTVecOut, TTOp, SolverParams, SolverInfo, MODE_FP64, MODE_FP32,
+                   MODE_TF32, TTError, check, LIB_PATH)
+
+__all__ = ["TT", "tt_matvec", "tt_sketch", "tt_dot", "tt_round_rand", "tt_gaussian", "tt_qr_f64",
+           "tt_lstsq_f64", "tt_sgmres_solve", "MODE_FP64", "MODE_FP32", "MODE_TF32", "TTError",
+           "LIB_PATH", "mode_dtype", "op_to_device"]
+
+
+def mode_dtype(mode: int) -> torch.dtype:
+    """Core dtype used by ``mode``."""
+    return torch.float64 if mode == MODE_FP64 else torch.float32
+
+
+class TT:
+    """A TT vector on the device: ``cores[k]`` has shape ``[r_{k-1}, n_k, r_k]``."""
+
+    def __init__(self, cores: Sequence[torch.Tensor]):
+        self.cores = [c.contiguous() for c in cores]
+
+    @property
+    def d(self) -> int:
+        return len(self.cores)
+
+    @property
+    def ns(self) -> List[int]:
+        return [c.shape[1] for c in self.cores]
+
+    @property
+    def ranks(self) -> List[int]:
+        return [c.shape[0] for c in self.cores] + [self.cores[-1].shape[2]]
+
+    @classmethod
+    def from_numpy(cls, cores, dtype=torch.float64, device="cuda"):
+        return cls([torch.as_tensor(c, dtype=dtype, device=device) for c in cores])
+
+    def numpy(self):
+        return [c.detach().double().cpu().numpy() for c in self.cores]
+
+    def to(self, dtype):
+        return TT([c.to(dtype) for c in self.cores])
+
+    def _desc(self):
+        d = self.d
+        n = (ctypes.c_int64 * d)(*self.ns)
+        r = (ctypes.c_int64 * (d + 1))(*self.ranks)
+        p = (ctypes.c_void_p * d)(*[c.data_ptr() for c in self.cores])
+        keep = (n, r, p)
+        return TTVec(d, n, r, p), keep
+
+
+def op_to_device(op, dtype=torch.float64, device="cuda"):
+    return [torch.as_tensor(c, dtype=dtype, device=device).contiguous() for c in op]
+
+
+def _op_desc(op):
+    d = len(op)
+    n = (ctypes.c_int64 * d)(*[c.shape[1] for c in op])
+    r = (ctypes.c_int64 * (d + 1))(*([c.shape[0] for c in op] + [op[-1].shape[3]]))
+    p = (ctypes.c_void_p * d)(*[c.data_ptr() for c in op])
+    return TTOp(d, n, r, p), (n, r, p)
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _workspace(nbytes: int, device):
+    return torch.empty(max(int(nbytes), 1), dtype=torch.uint8, device=device)
+
+
+def _check_dtype(tensors, mode):
+    want = mode_dtype(mode)
+    for t in tensors:
+        if t.dtype != want or not t.is_cuda or not t.is_contiguous():
+            raise TTError(1, f"expected contiguous CUDA {want} tensors for mode {mode}")
+
+
+def tt_matvec(op, x: TT, mode: int = MODE_FP64, stream=None) -> TT:
+    """``A x`` without truncation; output ranks ``R_k r_k``."""
+    _check_dtype(list(op) + x.cores, mode)
+    R = [c.shape[0] for c in op] + [1]
+    yr = [a * b for a, b in zip(R, x.ranks)]
+    y = TT([torch.empty((yr[k], x.ns[k], yr[k + 1]), dtype=x.cores[0].dtype,
+                        device=x.cores[0].device) for k in range(x.d)])
+    od, k1 = _op_desc(op)
+    xd, k2 = x._desc()
+    yd, k3 = y._desc()
+    ws = _workspace(lib.tt_matvec_workspace(mode, ctypes.byref(od), ctypes.byref(xd)),
+                    x.cores[0].device)
+    check(lib.tt_matvec(mode, ctypes.byref(od), ctypes.byref(xd), ctypes.byref(yd),
+                        ctypes.c_void_p(ws.data_ptr()), ws.numel(), _stream(stream)))
+    return y
+
+
+def tt_sketch(x: TT, S: Sequence[torch.Tensor], mode: int = MODE_FP64, stream=None) -> torch.Tensor:
+    """Khatri-Rao sketch ``S_odot x`` (float64 vector of length s)."""
+    _check_dtype(list(S) + x.cores, mode)
+    s = S[0].shape[0]
+    out = torch.empty(s, dtype=torch.float64, device=x.cores[0].device)
+    xd, k1 = x._desc()
+    Sp = (ctypes.c_void_p * x.d)(*[t.data_ptr() for t in S])
+    ws = _workspace(lib.tt_sketch_workspace(mode, ctypes.byref(xd), s), out.device)
+    check(lib.tt_sketch(mode, ctypes.byref(xd), s, Sp, ctypes.c_void_p(out.data_ptr()),
+                        ctypes.c_void_p(ws.data_ptr()), ws.numel(), _stream(stream)))
+    return out
+
+
+def tt_dot(x: TT, y: TT, mode: int = MODE_FP64, stream=None) -> torch.Tensor:
+    """``<x, y>`` as a one-element float64 device tensor."""
+    _check_dtype(x.cores + y.cores, mode)
+    out = torch.empty(1, dtype=torch.float64, device=x.cores[0].device)
+    xd, k1 = x._desc()
+    yd, k2 = y._desc()
+    ws = _workspace(lib.tt_dot_workspace(mode, ctypes.byref(xd), ctypes.byref(yd)), out.device)
+    check(lib.tt_dot(mode, ctypes.byref(xd), ctypes.byref(yd), ctypes.c_void_p(out.data_ptr()),
+                     ctypes.c_void_p(ws.data_ptr()), ws.numel(), _stream(stream)))
+    return out
+
+
+def tt_round_rand(terms: Sequence[TT], coefs: Sequence[float], eps: float, rmax: int,
+                  oversample: int = 10, seed: int = 0, drm=None, mode: int = MODE_FP64,
+                  stream=None) -> TT:
+    """Randomize-then-orthogonalize rounding of ``sum_b coefs[b] * terms[b]``.
+
+    ``drm``: ``None`` (Philox TT-DRM from ``seed``) or a list of DRM cores
+    ``[L_{k-1}, n_k, L_k]`` whose ranks cover the sketch ranks."""
+    allc = [c for t in terms for c in t.cores] + (list(drm) if drm is not None else [])
+    _check_dtype(allc, mode)
+    nt = len(terms)
+    descs, keep = [], []
+    for t in terms:
+        dsc, k = t._desc()
+        descs.append(dsc)
+        keep.append(k)
+    arr = (TTVec * nt)(*descs)
+    coef = (ctypes.c_double * nt)(*[float(c) for c in coefs])
+    d = terms[0].d
+    ns = terms[0].ns
+    dev = terms[0].cores[0].device
+    dt = terms[0].cores[0].dtype
+    # output capacities: min(rmax, summed rank) per bond is always enough
+    tsum = [sum(t.ranks[k] for t in terms) for k in range(d + 1)]
+    cap = [1] + [min(int(rmax), tsum[k]) if True else 0 for k in range(1, d)] + [1]
+    # the randomized sketch rank can exceed rmax before truncation only when eps == 0 and rmax
+    # >= sketch rank, in which case cap = min(rmax, t) still covers it
+    ycores = [torch.empty(cap[k] * ns[k] * cap[k + 1], dtype=dt, device=dev) for k in range(d)]
+    n_arr = (ctypes.c_int64 * d)(*ns)
+    cap_arr = (ctypes.c_int64 * (d + 1))(*cap)
+    rank_arr = (ctypes.c_int64 * (d + 1))()
+    yptr = (ctypes.c_void_p * d)(*[c.data_ptr() for c in ycores])
+    yd = TTVecOut(d, n_arr, cap_arr, rank_arr, yptr)
+    if drm is not None:
+        drm_p = (ctypes.c_void_p * d)(*[c.data_ptr() for c in drm])
+        drm_r = (ctypes.c_int64 * (d + 1))(*([c.shape[0] for c in drm] + [1]))
+    else:
+        drm_p, drm_r = None, None
+    ws = _workspace(lib.tt_round_rand_workspace(mode, nt, arr, int(rmax), int(oversample)), dev)
+    check(lib.tt_round_rand(mode, nt, arr, coef, float(eps), int(rmax), int(oversample),
+                            ctypes.c_uint64(seed), drm_p, drm_r, ctypes.byref(yd),
+                            ctypes.c_void_p(ws.data_ptr()), ws.numel(), _stream(stream)))
+    r = list(rank_arr)
+    return TT([ycores[k][: r[k] * ns[k] * r[k + 1]].view(r[k], ns[k], r[k + 1]) for k in range(d)])
+
+
+def tt_gaussian(count: int, seed: int, stream_id: int, std: float = 1.0,
+                mode: int = MODE_FP64, device="cuda", stream=None) -> torch.Tensor:
+    """Philox4x32-10 Gaussian stream elements ``0..count-1`` times ``std``."""
+    out = torch.empty(count, dtype=mode_dtype(mode), device=device)
+    check(lib.tt_gaussian(mode, ctypes.c_void_p(out.data_ptr()), count, ctypes.c_uint64(seed),
+                          ctypes.c_uint64(stream_id), float(std), _stream(stream)))
+    return out
+
+
+def tt_qr_f64(Y: torch.Tensor, want_q: bool = True, stream=None):
+    """FP64 Householder QR of a tall matrix (``m x l``, float64 or float32):
+    returns ``(Q, R)`` with Q in Y's dtype and R float64."""
+    mode = MODE_FP64 if Y.dtype == torch.float64 else MODE_FP32
+    m, l = Y.shape
+    Q = torch.empty((m, l), dtype=Y.dtype, device=Y.device) if want_q else None
+    R = torch.empty((l, l), dtype=torch.float64, device=Y.device)
+    ws = _workspace(lib.tt_qr_f64_workspace(m, l), Y.device)
+    check(lib.tt_qr_f64(mode, ctypes.c_void_p(Y.data_ptr()), m, l, Y.stride(0), Y.stride(1),
+                        ctypes.c_void_p(Q.data_ptr() if Q is not None else 0),
+                        ctypes.c_void_p(R.data_ptr()), ctypes.c_void_p(ws.data_ptr()), ws.numel(),
+                        _stream(stream)))
+    return Q, R
+
+
+def tt_lstsq_f64(W: torch.Tensor, c: torch.Tensor, stream=None):
+    """``y = argmin ||W y - c||`` (W: s x k float64) and ``||W y - c||``."""
+    s, k = W.shape
+    Wc = W.t().contiguous()  # column-major storage
+    y = torch.empty(k, dtype=torch.float64, device=W.device)
+    res = torch.empty(1, dtype=torch.float64, device=W.device)
+    ws = _workspace(lib.tt_lstsq_f64_workspace(s, k), W.device)
+    check(lib.tt_lstsq_f64(ctypes.c_void_p(Wc.data_ptr()), s, k,
+                           ctypes.c_void_p(c.contiguous().data_ptr()), ctypes.c_void_p(y.data_ptr()),
+                           ctypes.c_void_p(res.data_ptr()), ctypes.c_void_p(ws.data_ptr()),
+                           ws.numel(), _stream(stream)))
+    return y, res
+
+
+def tt_sgmres_solve(op, b: TT, maxit: int, tol: float, rmax: int, mode: int = MODE_FP64,
+                    s: int = 0, round_tol: float = 0.0, eta: float = 0.1,
+                    stop_safety: float = 0.1, r_sol: int = 0, oversample: int = 10, seed: int = 0,
+                    max_restarts: int = 5, hist_cap: int = 1024, workspace=None, stream=None,
+                    raise_on_nonconvergence: bool = False):
+    """Restarted TT-sGMRES.  ``op`` and ``b`` in float64 on the device.
+    Returns ``(x, info)``; ``x`` is a float64 :class:`TT`."""
+    _check_dtype(list(op) + b.cores, MODE_FP64)
+    p = SolverParams(maxit, s, tol, round_tol, eta, stop_safety, rmax, r_sol, oversample, seed,
+                     max_restarts, mode)
+    od, k1 = _op_desc(op)
+    bd, k2 = b._desc()
+    dev = b.cores[0].device
+    need = lib.tt_sgmres_solve_workspace(ctypes.byref(od), ctypes.byref(bd), ctypes.byref(p))
+    if need == 0:
+        raise TTError(1, lib.tt_last_error().decode())
+    if workspace is None or workspace.numel() < need:
+        workspace = _workspace(need, dev)
+    d = b.d
+    rs = r_sol if r_sol > 0 else rmax
+    cap = [1] + [rs] * (d - 1) + [1]
+    xc = [torch.empty(cap[k] * b.ns[k] * cap[k + 1], dtype=torch.float64, device=dev)
+          for k in range(d)]
+    n_arr = (ctypes.c_int64 * d)(*b.ns)
+    cap_arr = (ctypes.c_int64 * (d + 1))(*cap)
+    rank_arr = (ctypes.c_int64 * (d + 1))()
+    xp = (ctypes.c_void_p * d)(*[c.data_ptr() for c in xc])
+    xd = TTVecOut(d, n_arr, cap_arr, rank_arr, xp)
+    rh = (ctypes.c_double * hist_cap)()
+    kh = (ctypes.c_int64 * hist_cap)()
+    info = SolverInfo()
+    info.res_hist = ctypes.cast(rh, ctypes.POINTER(ctypes.c_double))
+    info.rank_hist = ctypes.cast(kh, ctypes.POINTER(ctypes.c_int64))
+    info.hist_cap = hist_cap
+    rc = lib.tt_sgmres_solve(ctypes.byref(od), ctypes.byref(bd), ctypes.byref(p),
+                             ctypes.byref(xd), ctypes.byref(info),
+                             ctypes.c_void_p(workspace.data_ptr()), workspace.numel(),
+                             _stream(stream))
+    if rc not in (0, 5) or (rc == 5 and raise_on_nonconvergence):
+        check(rc)
+    r = list(rank_arr)
+    x = TT([xc[k][: r[k] * b.ns[k] * r[k + 1]].view(r[k], b.ns[k], r[k + 1]) for k in range(d)])
+    n = min(info.iters, hist_cap)
+    out = dict(iters=info.iters, cycles=info.cycles, sketched_res=info.sketched_res,
+               true_res=info.true_res, max_rank=info.max_rank, status=info.status,
+               seconds=info.seconds, res_hist=list(rh[:n]), rank_hist=list(kh[:n]),
+               svd_nonconverged=info.svd_nonconverged,
+               workspace_bytes=int(need))
+    return x, out

@@ -1,0 +1,462 @@
+// extern "C" entry points declared in include/ttsg.h: argument validation,
+// conversion of the plain C descriptors into device views, workspace carving,
+// and translation of exceptions into status codes.
+#include "solver.cuh"
+#include <chrono>
+#include <cmath>
+
+namespace ttsg {
+
+thread_local bool g_dry_run = false;
+
+namespace {
+thread_local std::string g_last_error;
+
+struct DryGuard {
+  bool old;
+  DryGuard() : old(g_dry_run) { g_dry_run = true; }
+  ~DryGuard() { g_dry_run = old; }
+};
+
+template <typename F>
+int guarded(F&& f) {
+  try {
+    f();
+    g_last_error.clear();
+    return TT_OK;
+  } catch (const Error& e) {
+    g_last_error = e.what();
+    return e.code;
+  } catch (const std::exception& e) {
+    g_last_error = e.what();
+    return TT_ERR_CUDA;
+  }
+}
+
+int check_mode(int mode) {
+  if (mode != TT_MODE_FP64 && mode != TT_MODE_FP32 && mode != TT_MODE_TF32)
+    throw Error(TT_ERR_ARG, "unknown mode " + std::to_string(mode));
+  return mode;
+}
+
+template <typename T>
+TTv<T> view(const tt_vec* v, const char* what) {
+  if (!v) throw Error(TT_ERR_ARG, std::string(what) + ": null descriptor");
+  if (v->d < 1 || v->d > MAXD) throw Error(TT_ERR_ARG, std::string(what) + ": d out of range");
+  if (!v->n || !v->rank || !v->core) throw Error(TT_ERR_ARG, std::string(what) + ": null array");
+  TTv<T> t;
+  t.d = v->d;
+  for (int k = 0; k <= v->d; ++k) t.r[k] = v->rank[k];
+  if (t.r[0] != 1 || t.r[v->d] != 1)
+    throw Error(TT_ERR_ARG, std::string(what) + ": boundary ranks must be 1");
+  for (int k = 0; k < v->d; ++k) {
+    t.n[k] = v->n[k];
+    if (t.n[k] < 1 || t.r[k + 1] < 1) throw Error(TT_ERR_ARG, std::string(what) + ": n, rank >= 1");
+    if (!v->core[k]) throw Error(TT_ERR_ARG, std::string(what) + ": null core pointer");
+    t.core[k] = (T*)v->core[k];
+  }
+  return t;
+}
+
+template <typename T>
+TTv<T> view_out(const tt_vec_out* v, const char* what, int64_t* cap) {
+  if (!v || !v->n || !v->cap || !v->rank || !v->core)
+    throw Error(TT_ERR_ARG, std::string(what) + ": null descriptor or array");
+  if (v->d < 1 || v->d > MAXD) throw Error(TT_ERR_ARG, std::string(what) + ": d out of range");
+  TTv<T> t;
+  t.d = v->d;
+  for (int k = 0; k <= v->d; ++k) cap[k] = v->cap[k];
+  for (int k = 0; k < v->d; ++k) {
+    t.n[k] = v->n[k];
+    t.core[k] = (T*)v->core[k];
+    if (!t.core[k]) throw Error(TT_ERR_ARG, std::string(what) + ": null core pointer");
+  }
+  return t;
+}
+
+template <typename T>
+TTop<T> view_op(const tt_op* A, int permute_expected) {
+  (void)permute_expected;
+  if (!A || !A->n || !A->rank || !A->core) throw Error(TT_ERR_ARG, "operator: null descriptor");
+  if (A->d < 1 || A->d > MAXD) throw Error(TT_ERR_ARG, "operator: d out of range");
+  TTop<T> o;
+  o.d = A->d;
+  for (int k = 0; k <= A->d; ++k) o.R[k] = A->rank[k];
+  if (o.R[0] != 1 || o.R[A->d] != 1) throw Error(TT_ERR_ARG, "operator: boundary ranks must be 1");
+  for (int k = 0; k < A->d; ++k) {
+    o.n[k] = A->n[k];
+    o.core[k] = (T*)A->core[k];
+    if (!o.core[k]) throw Error(TT_ERR_ARG, "operator: null core pointer");
+  }
+  return o;
+}
+
+void same_modes(const int64_t* a, const int64_t* b, int d, const char* what) {
+  for (int k = 0; k < d; ++k)
+    if (a[k] != b[k]) throw Error(TT_ERR_ARG, std::string(what) + ": mode sizes differ");
+}
+
+// Workspace carving: a small header (error flag + reduction scratch) first.
+struct Carved {
+  Arena ar;
+  Ctx ctx;
+};
+Carved carve(int mode, void* ws, size_t bytes, void* stream, bool dry, bool with_gemm = true) {
+  Carved c;
+  c.ar = Arena(ws, bytes, dry);
+  if (!dry && !ws) throw Error(TT_ERR_WORKSPACE, "null workspace");
+  c.ctx.mode = mode;
+  c.ctx.st = (cudaStream_t)stream;
+  c.ctx.err = c.ar.take<int>(64);
+  c.ctx.scratch = c.ar.take<double>(512);
+  if (with_gemm) set_gemm_scratch(c.ar.take<char>((int64_t)GEMM_SCRATCH_BYTES), GEMM_SCRATCH_BYTES);
+  else set_gemm_scratch(nullptr, 0);
+  return c;
+}
+void reset_flags(Carved& c) {
+  if (!g_dry_run) TT_CUDA(cudaMemsetAsync(c.ctx.err, 0, 64 * sizeof(int), c.ctx.st));
+}
+void fix_ctx(Carved& c) { c.ctx.ar = &c.ar; }
+
+template <typename T>
+void permute_op(Carved& cv, const TTop<T>& in, TTop<T>& out) {
+  out.d = in.d;
+  std::vector<CopySeg> segs;
+  for (int k = 0; k < in.d; ++k) {
+    const int64_t R0 = in.R[k], R1 = in.R[k + 1], n = in.n[k];
+    out.n[k] = n;
+    out.R[k] = R0;
+    out.core[k] = cv.ar.take<T>(R0 * n * n * R1);
+    CopySeg s;
+    s.src = in.core[k]; s.dst = out.core[k];
+    s.A = R0 * n; s.B = R1; s.C = n; s.sa = n * R1; s.sb = 1; s.sc = R1;
+    s.src_f64 = s.dst_f64 = sizeof(T) == 8;
+    segs.push_back(s);
+  }
+  out.R[in.d] = 1;
+  copy3d(segs, cv.ctx.st);
+}
+
+template <typename T>
+void do_matvec(int mode, const tt_op* A, const tt_vec* x, const tt_vec* y, void* ws, size_t bytes,
+               void* stream, bool dry) {
+  TTop<T> a = view_op<T>(A, 0);
+  TTv<T> xv = view<T>(x, "x");
+  TTv<T> yv = view<T>(y, "y");
+  if (a.d != xv.d || yv.d != xv.d) throw Error(TT_ERR_ARG, "matvec: d mismatch");
+  same_modes(a.n, xv.n, xv.d, "matvec");
+  same_modes(yv.n, xv.n, xv.d, "matvec");
+  for (int k = 0; k <= xv.d; ++k)
+    if (yv.r[k] != a.R[k] * xv.r[k]) throw Error(TT_ERR_ARG, "matvec: y ranks must be R_k r_k");
+  Carved cv = carve(mode, ws, bytes, stream, dry);
+  fix_ctx(cv);
+  TTop<T> ap;
+  permute_op<T>(cv, a, ap);
+  tt_matvec_dev<T>(cv.ctx, ap, xv, yv);
+  if (dry) throw (size_t)cv.ar.peak;
+}
+
+template <typename F>
+size_t measure(F&& f) {
+  DryGuard g;
+  try {
+    f();
+  } catch (size_t peak) {
+    // margin for allocations whose size the dry run bounds from below
+    return peak + peak / 32 + (16u << 20);
+  } catch (const Error& e) {
+    g_last_error = e.what();
+    return 0;
+  }
+  return 0;
+}
+
+}  // namespace
+}  // namespace ttsg
+
+using namespace ttsg;
+
+// The definitions below keep the C linkage of their declarations in ttsg.h.
+
+const char* tt_version(void) { return "ttsg 0.1 (sm_103a)"; }
+const char* tt_last_error(void) { return g_last_error.c_str(); }
+
+size_t tt_matvec_workspace(int mode, const tt_op* A, const tt_vec* x) {
+  return measure([&] {
+    check_mode(mode);
+    // y descriptor with the product ranks
+    std::vector<int64_t> yr(x->d + 1);
+    for (int k = 0; k <= x->d; ++k) yr[k] = A->rank[k] * x->rank[k];
+    std::vector<void*> cores(x->d, (void*)1);
+    tt_vec y{x->d, x->n, yr.data(), cores.data()};
+    if (mode == TT_MODE_FP64) do_matvec<double>(mode, A, x, &y, nullptr, 0, nullptr, true);
+    else do_matvec<float>(mode, A, x, &y, nullptr, 0, nullptr, true);
+  });
+}
+
+int tt_matvec(int mode, const tt_op* A, const tt_vec* x, const tt_vec* y, void* ws,
+              size_t ws_bytes, void* stream) {
+  return guarded([&] {
+    check_mode(mode);
+    if (mode == TT_MODE_FP64) do_matvec<double>(mode, A, x, y, ws, ws_bytes, stream, false);
+    else do_matvec<float>(mode, A, x, y, ws, ws_bytes, stream, false);
+  });
+}
+
+namespace {
+template <typename T>
+void do_sketch(int mode, const tt_vec* x, int64_t s, void* const* S, double* out, void* ws,
+               size_t bytes, void* stream, bool dry) {
+  TTv<T> xv = view<T>(x, "x");
+  if (s < 1) throw Error(TT_ERR_ARG, "sketch: s >= 1");
+  if (!dry && (!S || !out)) throw Error(TT_ERR_ARG, "sketch: null S or out");
+  Carved cv = carve(mode, ws, bytes, stream, dry);
+  fix_ctx(cv);
+  std::vector<const T*> Sv(xv.d);
+  for (int k = 0; k < xv.d; ++k) {
+    Sv[k] = dry ? nullptr : (const T*)S[k];
+    if (!dry && !Sv[k]) throw Error(TT_ERR_ARG, "sketch: null factor");
+  }
+  tt_sketch_dev<T>(cv.ctx, xv, s, Sv.data(), out);
+  if (dry) throw (size_t)cv.ar.peak;
+}
+
+template <typename T>
+void do_dot(int mode, const tt_vec* x, const tt_vec* y, double* out, void* ws, size_t bytes,
+            void* stream, bool dry) {
+  TTv<T> xv = view<T>(x, "x");
+  TTv<T> yv = view<T>(y, "y");
+  if (xv.d != yv.d) throw Error(TT_ERR_ARG, "dot: d mismatch");
+  same_modes(xv.n, yv.n, xv.d, "dot");
+  if (!dry && !out) throw Error(TT_ERR_ARG, "dot: null out");
+  Carved cv = carve(mode, ws, bytes, stream, dry);
+  fix_ctx(cv);
+  tt_dot_dev<T>(cv.ctx, xv, yv, out);
+  if (dry) throw (size_t)cv.ar.peak;
+}
+
+template <typename T>
+void do_round(int mode, int nterms, const tt_vec* terms, const double* coef, double eps,
+              int64_t rmax, int64_t p, uint64_t seed, void* const* drm, const int64_t* drm_rank,
+              const tt_vec_out* y, void* ws, size_t bytes, void* stream, bool dry) {
+  if (nterms < 1 || !terms) throw Error(TT_ERR_ARG, "round: nterms >= 1");
+  if (!(eps >= 0.0) || rmax < 1 || p < 0) throw Error(TT_ERR_ARG, "round: eps >= 0, rmax >= 1, p >= 0");
+  std::vector<Term<T>> tv(nterms);
+  for (int b = 0; b < nterms; ++b) {
+    tv[b].X = view<T>(&terms[b], "term");
+    tv[b].coef = coef ? coef[b] : 1.0;
+    if (tv[b].X.d != tv[0].X.d) throw Error(TT_ERR_ARG, "round: d mismatch");
+    same_modes(tv[b].X.n, tv[0].X.n, tv[0].X.d, "round");
+  }
+  const int d = tv[0].X.d;
+  if (d < 2) throw Error(TT_ERR_ARG, "round: d >= 2");
+  int64_t ell[MAXD + 1];
+  std::vector<const int64_t*> tr;
+  for (auto& t : tv) tr.push_back(t.X.r);
+  rto_ranks(tr, tv[0].X.n, d, rmax, p, ell);
+  DRMSource<T> ds;
+  ds.seed = seed;
+  std::vector<const T*> dc(d);
+  if (drm) {
+    if (!drm_rank) throw Error(TT_ERR_ARG, "round: drm_rank required with drm");
+    for (int k = 0; k < d; ++k) dc[k] = (const T*)drm[k];
+    for (int k = 0; k <= d; ++k) ds.L[k] = drm_rank[k];
+    ds.core = dc.data();
+  } else {
+    for (int k = 0; k <= d; ++k) ds.L[k] = (k == 0 || k == d) ? 1 : rmax + p;
+  }
+  TTv<T> yv;
+  int64_t cap[MAXD + 1];
+  if (dry) {
+    yv.d = d;
+    for (int k = 0; k < d; ++k) yv.n[k] = tv[0].X.n[k];
+  } else {
+    yv = view_out<T>(y, "y", cap);
+    if (yv.d != d) throw Error(TT_ERR_ARG, "round: output d mismatch");
+    // output ranks are at most min(rmax, l_mu); capacities must cover that
+    for (int k = 1; k < d; ++k)
+      if (cap[k] < std::min<int64_t>(rmax, ell[k]))
+        throw Error(TT_ERR_ARG, "round: output capacity below min(rmax, sketch rank)");
+  }
+  Carved cv = carve(mode, ws, bytes, stream, dry);
+  fix_ctx(cv);
+  reset_flags(cv);
+  tt_round_rand_dev<T>(cv.ctx, tv, eps, rmax, p, ds, yv);
+  if (dry) throw (size_t)cv.ar.peak;
+  for (int k = 0; k <= d; ++k) y->rank[k] = yv.r[k];
+}
+}  // namespace
+
+size_t tt_sketch_workspace(int mode, const tt_vec* x, int64_t s) {
+  return measure([&] {
+    check_mode(mode);
+    if (mode == TT_MODE_FP64) do_sketch<double>(mode, x, s, nullptr, nullptr, nullptr, 0, nullptr, true);
+    else do_sketch<float>(mode, x, s, nullptr, nullptr, nullptr, 0, nullptr, true);
+  });
+}
+
+int tt_sketch(int mode, const tt_vec* x, int64_t s, void* const* S, double* out, void* ws,
+              size_t ws_bytes, void* stream) {
+  return guarded([&] {
+    check_mode(mode);
+    if (mode == TT_MODE_FP64) do_sketch<double>(mode, x, s, S, out, ws, ws_bytes, stream, false);
+    else do_sketch<float>(mode, x, s, S, out, ws, ws_bytes, stream, false);
+  });
+}
+
+size_t tt_dot_workspace(int mode, const tt_vec* x, const tt_vec* y) {
+  return measure([&] {
+    check_mode(mode);
+    if (mode == TT_MODE_FP64) do_dot<double>(mode, x, y, nullptr, nullptr, 0, nullptr, true);
+    else do_dot<float>(mode, x, y, nullptr, nullptr, 0, nullptr, true);
+  });
+}
+
+int tt_dot(int mode, const tt_vec* x, const tt_vec* y, double* out, void* ws, size_t ws_bytes,
+           void* stream) {
+  return guarded([&] {
+    check_mode(mode);
+    if (mode == TT_MODE_FP64) do_dot<double>(mode, x, y, out, ws, ws_bytes, stream, false);
+    else do_dot<float>(mode, x, y, out, ws, ws_bytes, stream, false);
+  });
+}
+
+size_t tt_round_rand_workspace(int mode, int nterms, const tt_vec* terms, int64_t rmax,
+                               int64_t oversample) {
+  return measure([&] {
+    check_mode(mode);
+    if (mode == TT_MODE_FP64)
+      do_round<double>(mode, nterms, terms, nullptr, 0.1, rmax, oversample, 0, nullptr, nullptr,
+                       nullptr, nullptr, 0, nullptr, true);
+    else
+      do_round<float>(mode, nterms, terms, nullptr, 0.1, rmax, oversample, 0, nullptr, nullptr,
+                      nullptr, nullptr, 0, nullptr, true);
+  });
+}
+
+int tt_round_rand(int mode, int nterms, const tt_vec* terms, const double* coef, double eps,
+                  int64_t rmax, int64_t oversample, uint64_t seed, void* const* drm,
+                  const int64_t* drm_rank, const tt_vec_out* y, void* ws, size_t ws_bytes,
+                  void* stream) {
+  return guarded([&] {
+    check_mode(mode);
+    if (mode == TT_MODE_FP64)
+      do_round<double>(mode, nterms, terms, coef, eps, rmax, oversample, seed, drm, drm_rank, y,
+                       ws, ws_bytes, stream, false);
+    else
+      do_round<float>(mode, nterms, terms, coef, eps, rmax, oversample, seed, drm, drm_rank, y, ws,
+                      ws_bytes, stream, false);
+  });
+}
+
+int tt_gaussian(int mode, void* out, int64_t count, uint64_t seed, uint64_t stream_id, double std_,
+                void* stream) {
+  return guarded([&] {
+    check_mode(mode);
+    if (count < 0 || (count > 0 && !out)) throw Error(TT_ERR_ARG, "gaussian: bad output");
+    gaussian_fill(out, mode == TT_MODE_FP64, count, seed, stream_id, std_, (cudaStream_t)stream);
+  });
+}
+
+size_t tt_qr_f64_workspace(int64_t m, int64_t l) { return qr_workspace(m, l) + 64 * 1024; }
+
+int tt_qr_f64(int mode, const void* Y, int64_t m, int64_t l, int64_t sr, int64_t sc, void* Q,
+              double* R, void* ws, size_t ws_bytes, void* stream) {
+  return guarded([&] {
+    check_mode(mode);
+    if (!Y || m < l || l < 1) throw Error(TT_ERR_ARG, "qr: need Y and m >= l >= 1");
+    Carved cv = carve(mode, ws, ws_bytes, stream, false, false);
+    fix_ctx(cv);
+    reset_flags(cv);
+    const size_t rest = ws_bytes - cv.ar.mark();
+    void* qw = cv.ar.take<char>((int64_t)qr_workspace(m, l));
+    const int f64 = mode == TT_MODE_FP64;
+    qr_f64(Y, f64, m, l, sr, sc, Q, f64, l, R, qw, rest, cv.ctx.err, cv.ctx.st);
+    check_device_flags(cv.ctx);
+  });
+}
+
+size_t tt_lstsq_f64_workspace(int64_t s, int64_t k) { return lstsq_workspace(s, k) + 4096; }
+
+int tt_lstsq_f64(const double* W, int64_t s, int64_t k, const double* c, double* y, double* res,
+                 void* ws, size_t ws_bytes, void* stream) {
+  return guarded([&] {
+    if (!W || !c || !y || !res || !ws || s < 1 || k < 1 || k > s)
+      throw Error(TT_ERR_ARG, "lstsq: bad arguments");
+    if (ws_bytes < lstsq_workspace(s, k)) throw Error(TT_ERR_WORKSPACE, "lstsq: workspace");
+    cudaStream_t st = (cudaStream_t)stream;
+    lstsq_reset(c, s, k, ws, st);
+    for (int64_t j = 0; j < k; ++j) lstsq_add_column(W, c, s, j, k, ws, y, res, st);
+  });
+}
+
+namespace {
+SolveParams to_params(const tt_solver_params* p) {
+  if (!p) throw Error(TT_ERR_ARG, "solve: null params");
+  SolveParams q;
+  q.maxit = p->maxit; q.s = p->s; q.tol = p->tol; q.round_tol = p->round_tol; q.eta = p->eta;
+  q.stop_safety = p->stop_safety; q.rmax = p->rmax; q.r_sol = p->r_sol;
+  q.oversample = p->oversample; q.seed = p->seed; q.max_restarts = p->max_restarts;
+  if (q.maxit < 1 || q.tol <= 0 || q.rmax < 1 || q.oversample < 0 || q.max_restarts < 0 ||
+      q.eta < 0 || q.stop_safety <= 0)
+    throw Error(TT_ERR_ARG, "solve: invalid parameters");
+  return q;
+}
+
+void do_solve(const tt_op* A, const tt_vec* b, const tt_solver_params* p, const tt_vec_out* x,
+              tt_solver_info* info, void* ws, size_t bytes, void* stream, bool dry) {
+  SolveParams q = to_params(p);
+  check_mode(p->mode);
+  TTop<double> a = view_op<double>(A, 0);
+  TTv<double> bv = view<double>(b, "b");
+  if (a.d != bv.d) throw Error(TT_ERR_ARG, "solve: d mismatch");
+  same_modes(a.n, bv.n, bv.d, "solve");
+  TTv<double> xv;
+  int64_t cap[MAXD + 1];
+  const int64_t r_sol = q.r_sol > 0 ? q.r_sol : q.rmax;
+  if (!dry) {
+    xv = view_out<double>(x, "x", cap);
+    if (xv.d != bv.d) throw Error(TT_ERR_ARG, "solve: x d mismatch");
+    for (int k = 1; k < bv.d; ++k)
+      if (cap[k] < r_sol) throw Error(TT_ERR_ARG, "solve: x capacity below r_sol");
+  } else {
+    xv.d = bv.d;
+  }
+  Carved cv = carve(p->mode, ws, bytes, stream, dry);
+  fix_ctx(cv);
+  reset_flags(cv);
+  SolveResult r = p->mode == TT_MODE_FP64 ? sgmres_solve<double>(cv.ctx, a, bv, q, xv)
+                                          : sgmres_solve<float>(cv.ctx, a, bv, q, xv);
+  if (dry) throw (size_t)cv.ar.peak;
+  for (int k = 0; k <= bv.d; ++k) x->rank[k] = xv.r[k];
+  if (info) {
+    info->iters = r.iters;
+    info->cycles = r.cycles;
+    info->sketched_res = r.sketched_res;
+    info->true_res = r.true_res;
+    info->max_rank = r.max_rank;
+    info->status = r.status;
+    info->seconds = r.seconds;
+    info->svd_nonconverged = r.svd_nonconverged;
+    for (int i = 0; i < info->hist_cap && i < (int)r.res_hist.size(); ++i) {
+      if (info->res_hist) info->res_hist[i] = r.res_hist[i];
+      if (info->rank_hist) info->rank_hist[i] = r.rank_hist[i];
+    }
+  }
+  if (r.status != TT_OK)
+    throw Error(TT_ERR_NOT_CONVERGED, "solve: true residual " + std::to_string(r.true_res) +
+                                          " above tol after " + std::to_string(r.cycles) +
+                                          " cycles");
+}
+}  // namespace
+
+size_t tt_sgmres_solve_workspace(const tt_op* A, const tt_vec* b, const tt_solver_params* p) {
+  return measure([&] { do_solve(A, b, p, nullptr, nullptr, nullptr, 0, nullptr, true); });
+}
+
+int tt_sgmres_solve(const tt_op* A, const tt_vec* b, const tt_solver_params* p,
+                    const tt_vec_out* x, tt_solver_info* info, void* ws, size_t ws_bytes,
+                    void* stream) {
+  return guarded([&] { do_solve(A, b, p, x, info, ws, ws_bytes, stream, false); });
+}
+

@@ -1,0 +1,341 @@
+// TT-sGMRES driver: Algorithm 4 with incomplete orthogonalisation l = 1 done
+// explicitly in TT format (the Remark of Section 3.6 for l = 1), randomized
+// rounding for the Gram-Schmidt update and for the final sum (Section 3.5),
+// y_k = (S A V_k)^+ S r_0 (eq. pseudo_inv) by the incremental FP64 QR, and the
+// restart loop of Section 3.4 driven by the exact FP64 true residual.
+//
+// Per iteration (all on the device; the host reads the new ranks and the
+// sketched residual once):
+//   w = A v_k (untruncated)  ->  W[:, k] = S w  ->  h = <w, v_k>
+//   v~ = Round(w - h v_k, round_tol, rmax)  ->  v_{k+1} = v~ / ||v~||
+//   y = argmin ||W y - S r0||, stop when ||W y - S r0|| <= inner_tol ||S r0||.
+#include "solver.cuh"
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+
+namespace ttsg {
+
+namespace {
+
+template <typename T>
+constexpr int f64_of() { return sizeof(T) == 8 ? 1 : 0; }
+
+double read_double(cudaStream_t st, const double* dev) {
+  if (g_dry_run) return 1.0;
+  double h = 0.0;
+  TT_CUDA(cudaMemcpyAsync(&h, dev, sizeof(double), cudaMemcpyDeviceToHost, st));
+  TT_CUDA(cudaStreamSynchronize(st));
+  return h;
+}
+
+// Mode-dependent floor of the per-cycle sketched tolerance: the accuracy the
+// contractions of that precision can deliver before a restart is needed.
+double inner_floor(int mode) {
+  switch (mode) {
+    case TT_MODE_FP64: return 0.0;
+    case TT_MODE_FP32: return 1e-5;
+    default: return 1e-3;
+  }
+}
+
+template <typename T>
+TTv<T> alloc_tt(Arena& ar, int d, const int64_t* n, const int64_t* cap) {
+  TTv<T> v;
+  v.d = d;
+  for (int k = 0; k < d; ++k) {
+    v.n[k] = n[k];
+    v.core[k] = ar.take<T>(cap[k] * n[k] * cap[k + 1]);
+    v.r[k] = cap[k];
+  }
+  v.r[d] = 1;
+  return v;
+}
+
+}  // namespace
+
+template <typename T>
+SolveResult sgmres_solve(const Ctx& c0, const TTop<double>& A64in, const TTv<double>& b,
+                         const SolveParams& p, TTv<double>& xout) {
+  Ctx c = c0;
+  Arena& ar = *c.ar;
+  const int d = b.d;
+  const int f64 = f64_of<T>();
+  const auto t_start = std::chrono::steady_clock::now();
+  TT_CHECK_ARG(d >= 2 && d <= MAXD, "solve: 2 <= d <= 64");
+  TT_CHECK_ARG(p.maxit >= 1 && p.rmax >= 1 && p.tol > 0, "solve: maxit, rmax, tol");
+  const int64_t s = p.s > 0 ? p.s : 2 * p.maxit;
+  const int64_t r_sol = p.r_sol > 0 ? p.r_sol : p.rmax;
+  const int64_t* n = b.n;
+  SolveResult res;
+
+  // ---- operator in the working layout [a][i][a'][j] (working and FP64 copies)
+  TTop<T> A;
+  TTop<double> A64;
+  A.d = A64.d = d;
+  int64_t Rmax = 1;
+  {
+    std::vector<CopySeg> segs;
+    for (int k = 0; k < d; ++k) {
+      const int64_t R0 = A64in.R[k], R1 = A64in.R[k + 1], nn = n[k];
+      A.n[k] = A64.n[k] = nn;
+      A.R[k] = A64.R[k] = R0;
+      Rmax = std::max(Rmax, R0);
+      A64.core[k] = ar.take<double>(R0 * nn * nn * R1);
+      A.core[k] = f64 ? (T*)A64.core[k] : ar.take<T>(R0 * nn * nn * R1);
+      CopySeg sg;
+      sg.src = A64in.core[k]; sg.dst = A64.core[k];
+      sg.A = R0 * nn; sg.B = R1; sg.C = nn; sg.sa = nn * R1; sg.sb = 1; sg.sc = R1;
+      sg.src_f64 = 1; sg.dst_f64 = 1;
+      segs.push_back(sg);
+      if (!f64) {
+        CopySeg s2 = sg;
+        s2.dst = A.core[k];
+        s2.dst_f64 = 0;
+        segs.push_back(s2);
+      }
+    }
+    A.R[d] = A64.R[d] = 1;
+    copy3d(segs, c.st);
+  }
+  // ---- Khatri-Rao factors S_k: N(0, s^{-1/d}), Philox streams 1024 + k
+  std::vector<T*> S(d);
+  for (int k = 0; k < d; ++k) {
+    S[k] = ar.take<T>(s * n[k]);
+    gaussian_fill(S[k], f64, s * n[k], p.seed, 1024 + (uint64_t)k, std::pow((double)s, -0.5 / d),
+                  c.st);
+  }
+  DRMSource<T> drm;
+  drm.seed = p.seed;
+  drm.L[0] = drm.L[d] = 1;
+  for (int k = 1; k < d; ++k) drm.L[k] = std::max(p.rmax, r_sol) + p.oversample;
+
+  // ---- persistent buffers
+  int64_t rb = 1;
+  for (int k = 0; k <= d; ++k) rb = std::max(rb, b.r[k]);
+  const int64_t vcap_r = std::max(p.rmax, rb);
+  std::vector<int64_t> vcap(d + 1, vcap_r), wcap(d + 1), xcap(d + 1, r_sol), bcap(d + 1);
+  vcap[0] = vcap[d] = 1;
+  xcap[0] = xcap[d] = 1;
+  for (int k = 0; k <= d; ++k) {
+    wcap[k] = A64.R[k] * std::max(vcap[k], xcap[k]);
+    bcap[k] = b.r[k];
+  }
+  std::vector<TTv<T>> V;
+  for (int i = 0; i <= p.maxit; ++i) V.push_back(alloc_tt<T>(ar, d, n, vcap.data()));
+  TTv<T> w = alloc_tt<T>(ar, d, n, wcap.data());
+  TTv<T> bT = f64 ? TTv<T>() : alloc_tt<T>(ar, d, n, bcap.data());
+  TTv<T> rhs = alloc_tt<T>(ar, d, n, vcap.data());
+  // the cycle's correction e is computed in the working precision; the
+  // accumulated solution, the residual b - A x and its rounding stay in FP64
+  // (mixed-precision iterative refinement)
+  TTv<T> e = alloc_tt<T>(ar, d, n, xcap.data());
+  TTv<double> x = alloc_tt<double>(ar, d, n, xcap.data());
+  TTv<double> xn = alloc_tt<double>(ar, d, n, xcap.data());
+  TTv<double> e64 = alloc_tt<double>(ar, d, n, xcap.data());
+  TTv<double> w64 = alloc_tt<double>(ar, d, n, wcap.data());
+  TTv<double> r64 = alloc_tt<double>(ar, d, n, vcap.data());
+  Ctx c64 = c;
+  c64.mode = TT_MODE_FP64;
+  DRMSource<double> drm64;
+  drm64.seed = drm.seed;
+  for (int k = 0; k <= d; ++k) drm64.L[k] = drm.L[k];
+  double* Wm = ar.take<double>(s * p.maxit);
+  double* Sr0 = ar.take<double>(s);
+  double* ydev = ar.take<double>(p.maxit);
+  double* scal = ar.take<double>(16);  // 0 beta, 1 h, 2 ||v~||^2, 3 ||v~||, 4 res, 5 ||Sr0||^2, 6 ||Sr0||
+  double* lsws = (double*)ar.take<char>((int64_t)lstsq_workspace(s, p.maxit));
+  if (f64) {
+    bT.d = d;
+    for (int k = 0; k < d; ++k) { bT.n[k] = n[k]; bT.core[k] = (T*)b.core[k]; }
+    for (int k = 0; k <= d; ++k) bT.r[k] = b.r[k];
+  } else {
+    std::vector<CopySeg> segs;
+    for (int k = 0; k < d; ++k) {
+      CopySeg sg;
+      sg.src = b.core[k]; sg.dst = bT.core[k]; sg.A = b.core_elems(k); sg.sa = 1;
+      sg.src_f64 = 1; sg.dst_f64 = 0;
+      segs.push_back(sg);
+      bT.r[k] = b.r[k];
+    }
+    bT.r[d] = 1;
+    copy3d(segs, c.st);
+  }
+
+  auto copy_tt = [&](const auto& src, auto& dst, const double* scale_dev, int inv) {
+    std::vector<CopySeg> segs;
+    for (int k = 0; k < d; ++k) {
+      CopySeg sg;
+      sg.src = src.core[k]; sg.dst = dst.core[k]; sg.A = src.core_elems(k); sg.sa = 1;
+      sg.src_f64 = sizeof(*src.core[0]) == 8; sg.dst_f64 = sizeof(*dst.core[0]) == 8;
+      if (k == 0) { sg.scale_dev = scale_dev; sg.scale_dev_inv = inv; }
+      segs.push_back(sg);
+      dst.r[k] = src.r[k];
+    }
+    dst.r[d] = 1;
+    copy3d(segs, c.st);
+  };
+
+  if (g_dry_run) {
+    // workspace query: run every scratch-using step once at capacity ranks
+    for (auto& v : V) for (int q = 0; q <= d; ++q) v.r[q] = vcap[q];
+    for (int q = 0; q <= d; ++q) { w.r[q] = wcap[q]; x.r[q] = e.r[q] = xcap[q]; }
+    tt_dot_dev<double>(Ctx{TT_MODE_FP64, c.st, c.ar, c.err, c.scratch}, b, b, scal + 8);
+    tt_sketch_dev<T>(c, w, s, (const T* const*)S.data(), Wm);
+    tt_dot_dev<T>(c, w, V[0], scal + 1);
+    std::vector<Term<T>> t2(2);
+    t2[0].X = w; t2[1].X = V[0];
+    tt_round_rand_dev<T>(c, t2, 0.1, p.rmax, p.oversample, drm, V[1]);
+    std::vector<Term<T>> tk(p.maxit);
+    for (int i = 0; i < p.maxit; ++i) tk[i].X = V[i];
+    tt_round_rand_dev<T>(c, tk, 0.1, r_sol, p.oversample, drm, e);
+    for (int q = 0; q <= d; ++q) { e64.r[q] = xcap[q]; w64.r[q] = wcap[q]; }
+    std::vector<Term<double>> u2(2);
+    u2[0].X = x; u2[1].X = e64;
+    tt_round_rand_dev<double>(c64, u2, 0.1, r_sol, p.oversample, drm64, xn);
+    true_residual_norm<double>(c, A64, b, x);
+    u2[0].X = b; u2[1].X = w64;
+    tt_round_rand_dev<double>(c64, u2, 0.1, p.rmax, p.oversample, drm64, r64);
+    return res;
+  }
+  // ||b|| in FP64 by the Gram sweep
+  tt_dot_dev<double>(Ctx{TT_MODE_FP64, c.st, c.ar, c.err, c.scratch}, b, b, scal + 8);
+  const double b2 = read_double(c.st, scal + 8);
+  const double bn = std::sqrt(std::max(b2, 0.0));
+  TT_CHECK_ARG(bn > 0.0, "solve: b is zero");
+
+  double rel = 1.0;
+  bool have_x = false;
+  const TTv<T>* cur_rhs = &bT;
+  for (int cyc = 0; cyc <= p.max_restarts; ++cyc) {
+    double inner = std::min(0.5, p.stop_safety * p.tol / rel);
+    inner = std::max(inner, inner_floor(c.mode));
+    const double round_tol = p.round_tol > 0 ? p.round_tol : p.eta * inner;
+    const double final_tol = 0.01 * p.tol;
+    // v_1 = r0 / ||r0||, S r0, ||S r0||
+    tt_dot_dev<T>(c, *cur_rhs, *cur_rhs, scal + 0);
+    sqrt_scalar(scal + 0, scal + 0, c.st);
+    copy_tt(*cur_rhs, V[0], scal + 0, 1);
+    tt_sketch_dev<T>(c, *cur_rhs, s, (const T* const*)S.data(), Sr0);
+    sumsq(Sr0, 1, s, scal + 5, c.scratch + 16, c.st);
+    sqrt_scalar(scal + 5, scal + 6, c.st);
+    lstsq_reset(Sr0, s, p.maxit, lsws, c.st);
+    const double betaS = read_double(c.st, scal + 6);
+    int kdone = 0;
+    double sres = 1.0;
+    for (int k = 0; k < p.maxit; ++k) {
+      // w = A v_k
+      for (int q = 0; q <= d; ++q) w.r[q] = A64.R[q] * V[k].r[q];
+      tt_matvec_dev<T>(c, A, V[k], w);
+      // W[:, k] = S w
+      tt_sketch_dev<T>(c, w, s, (const T* const*)S.data(), Wm + k * s);
+      // h = <w, v_k>
+      tt_dot_dev<T>(c, w, V[k], scal + 1);
+      // v~ = Round(w - h v_k)
+      std::vector<Term<T>> terms(2);
+      terms[0].X = w;
+      terms[1].X = V[k];
+      terms[1].coef = -1.0;
+      terms[1].coef_dev = scal + 1;
+      tt_round_rand_dev<T>(c, terms, round_tol, p.rmax, p.oversample, drm, V[k + 1]);
+      // h_{k+1,k} = ||v~|| = ||core 1|| (cores 2..d are right-orthogonal)
+      sumsq(V[k + 1].core[0], f64, V[k + 1].core_elems(0), scal + 2, c.scratch + 16, c.st);
+      sqrt_scalar(scal + 2, scal + 3, c.st);
+      {
+        CopySeg sg;
+        sg.src = V[k + 1].core[0]; sg.dst = V[k + 1].core[0]; sg.A = V[k + 1].core_elems(0);
+        sg.sa = 1; sg.src_f64 = f64; sg.dst_f64 = f64; sg.scale_dev = scal + 3; sg.scale_dev_inv = 1;
+        copy3d({sg}, c.st);
+      }
+      lstsq_add_column(Wm, Sr0, s, k, p.maxit, lsws, ydev, scal + 4, c.st);
+      double hv[2] = {1.0, 1.0};
+      if (!g_dry_run) {
+        TT_CUDA(cudaMemcpyAsync(hv, scal + 3, 2 * sizeof(double), cudaMemcpyDeviceToHost, c.st));
+        TT_CUDA(cudaStreamSynchronize(c.st));
+      }
+      sres = betaS > 0 ? hv[1] / betaS : 0.0;
+      res.res_hist.push_back(sres);
+      res.rank_hist.push_back(V[k + 1].max_rank());
+      res.max_rank = std::max(res.max_rank, V[k + 1].max_rank());
+      kdone = k + 1;
+      ++res.iters;
+      if (hv[1] <= inner * betaS || hv[0] == 0.0) break;
+    }
+    // e = Round(sum_i y_i v_i)
+    {
+      std::vector<Term<T>> terms(kdone);
+      for (int i = 0; i < kdone; ++i) {
+        terms[i].X = V[i];
+        terms[i].coef = 1.0;
+        terms[i].coef_dev = ydev + i;
+      }
+      tt_round_rand_dev<T>(c, terms, final_tol, r_sol, p.oversample, drm, e);
+    }
+    // x <- Round(x + e) in FP64
+    if (!have_x) {
+      copy_tt(e, x, nullptr, 0);
+      have_x = true;
+    } else {
+      copy_tt(e, e64, nullptr, 0);
+      std::vector<Term<double>> terms(2);
+      terms[0].X = x;
+      terms[1].X = e64;
+      tt_round_rand_dev<double>(c64, terms, final_tol, r_sol, p.oversample, drm64, xn);
+      copy_tt(xn, x, nullptr, 0);
+    }
+    res.cycles = cyc + 1;
+    res.sketched_res = sres;
+    rel = true_residual_norm<double>(c, A64, b, x) / bn;
+    res.true_res = rel;
+    if (std::getenv("TTSG_DEBUG"))
+      std::fprintf(stderr, "[ttsg] cycle %d: %d its, sketched %.3e (target %.1e), true %.3e, "
+                   "x max rank %lld\n", cyc, kdone, sres, inner, rel, (long long)x.max_rank());
+    if (rel <= p.tol) break;
+    // next right-hand side: Round(b - A x), formed and rounded in FP64
+    for (int q = 0; q <= d; ++q) w64.r[q] = A64.R[q] * x.r[q];
+    tt_matvec_dev<double>(c64, A64, x, w64);
+    std::vector<Term<double>> terms(2);
+    terms[0].X = b;
+    terms[1].X = w64;
+    terms[1].coef = -1.0;
+    const double next_inner = std::max(std::min(0.5, p.stop_safety * p.tol / rel),
+                                       inner_floor(c.mode));
+    tt_round_rand_dev<double>(c64, terms, std::max(0.1 * next_inner, 1e-14), p.rmax,
+                              p.oversample, drm64, r64);
+    copy_tt(r64, rhs, nullptr, 0);
+    cur_rhs = &rhs;
+  }
+  // output in FP64
+  {
+    std::vector<CopySeg> segs;
+    xout.d = d;
+    for (int k = 0; k < d; ++k) {
+      CopySeg sg;
+      sg.src = x.core[k]; sg.dst = xout.core[k]; sg.A = x.core_elems(k); sg.sa = 1;
+      sg.src_f64 = 1; sg.dst_f64 = 1;
+      segs.push_back(sg);
+      xout.r[k] = x.r[k];
+      xout.n[k] = n[k];
+    }
+    xout.r[d] = 1;
+    copy3d(segs, c.st);
+    if (!g_dry_run) TT_CUDA(cudaStreamSynchronize(c.st));
+  }
+  if (!g_dry_run) {
+    int flags[2] = {0, 0};
+    TT_CUDA(cudaMemcpy(flags, c.err, sizeof(flags), cudaMemcpyDeviceToHost));
+    res.svd_nonconverged = flags[1];
+  }
+  res.status = res.true_res <= p.tol ? TT_OK : TT_ERR_NOT_CONVERGED;
+  res.seconds =
+      std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
+  return res;
+}
+
+template SolveResult sgmres_solve<float>(const Ctx&, const TTop<double>&, const TTv<double>&,
+                                         const SolveParams&, TTv<double>&);
+template SolveResult sgmres_solve<double>(const Ctx&, const TTop<double>&, const TTv<double>&,
+                                          const SolveParams&, TTv<double>&);
+
+}  // namespace ttsg

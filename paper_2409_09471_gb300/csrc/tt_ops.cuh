@@ -1,0 +1,65 @@
+// TT operations of the solver iteration, expressed as grouped GEMMs plus the
+// FP64 QR / Jacobi kernels.  All functions enqueue work on ctx.st; functions
+// that must learn data-dependent ranks synchronise that stream.
+#pragma once
+#include "kernels.cuh"
+
+namespace ttsg {
+
+struct Ctx {
+  int mode = TT_MODE_FP32;
+  cudaStream_t st = nullptr;
+  Arena* ar = nullptr;
+  int* err = nullptr;        // device flags: err[0] bit 0 = QR barrier timeout,
+                             // err[1] = Jacobi sweep-cap count
+  double* scratch = nullptr; // device scratch for reductions (>= 256 doubles)
+  bool f64() const { return mode == TT_MODE_FP64; }
+};
+
+// One term of an implicit sum: coef * (*coef_dev if set) * X.
+template <typename T>
+struct Term {
+  TTv<T> X;
+  double coef = 1.0;
+  const double* coef_dev = nullptr;
+};
+
+// Source of the Gaussian TT-DRM of a randomized rounding: explicit cores with
+// capacity ranks L, or the Philox stream (seed, 2048 + k) read as a virtual
+// array of capacity ranks L.
+template <typename T>
+struct DRMSource {
+  const T* const* core = nullptr;  // nullptr => Philox
+  int64_t L[MAXD + 1] = {};
+  uint64_t seed = 0;
+};
+
+template <typename T>
+void tt_matvec_dev(const Ctx& c, const TTop<T>& A, const TTv<T>& x, const TTv<T>& y);
+
+template <typename T>
+void tt_sketch_dev(const Ctx& c, const TTv<T>& x, int64_t s, const T* const* S, double* out);
+
+template <typename T>
+void tt_dot_dev(const Ctx& c, const TTv<T>& x, const TTv<T>& y, double* out);
+
+// Randomize-then-orthogonalize rounding of sum_b terms[b] into y (cores with
+// capacity; y.r[] is filled in).  Returns after a stream synchronisation.
+template <typename T>
+void tt_round_rand_dev(const Ctx& c, const std::vector<Term<T>>& terms, double eps, int64_t rmax,
+                       int64_t oversample, const DRMSource<T>& drm, TTv<T>& y);
+
+// Sketch ranks l_mu of the randomized rounding (see tt_round_rand).
+void rto_ranks(const std::vector<const int64_t*>& term_ranks, const int64_t* n, int d,
+               int64_t rmax, int64_t oversample, int64_t* ells);
+
+// Exact ||b - A x|| in FP64 (QR sweep of the explicit sum; A x is formed in
+// FP64).  x in the working precision, A and b in FP64 (A permuted layout).
+template <typename T>
+double true_residual_norm(const Ctx& c, const TTop<double>& A, const TTv<double>& b,
+                          const TTv<T>& x);
+
+// Raise TT_ERR_TIMEOUT if a device wait expired (synchronises).
+void check_device_flags(const Ctx& c);
+
+}  // namespace ttsg

@@ -1,0 +1,68 @@
+"""End-to-end GPU solves through the C ABI, checked against the oracle:
+dense fast-diagonalisation solutions where the grid is small enough, and the
+oracle's exact FP64 TT residual (plus the oracle's own TT-sGMRES iteration
+count) at full size."""
+import numpy as np
+import pytest
+import torch
+
+import ttinputs as ti
+from oracle import tt as ott, solvers as osol, philox as oph, closed_forms as cf
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def g():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2409_09471_gb300 as g
+    return g
+
+
+def solve(g, w, mode, **kw):
+    p = dict(w.params)
+    p.update(kw)
+    op = g.op_to_device(w.op)
+    b = g.TT.from_numpy(w.b)
+    return g.tt_sgmres_solve(op, b, maxit=p["maxit"], tol=p["tol"], rmax=p["rmax"], mode=mode,
+                             s=p.get("s", 0), round_tol=p.get("round_tol", 0.0),
+                             eta=p.get("eta", 0.1), stop_safety=p.get("stop_safety", 0.1),
+                             r_sol=p.get("r_sol", 0), oversample=p["oversample"], seed=p.get("seed", 0),
+                             max_restarts=p.get("max_restarts", 5))
+
+
+def test_laplace_fp64_config_vs_closed_form(g):
+    w = ti.workload("laplace_fp64")
+    x, info = solve(g, w, g.MODE_FP64, stop_safety=0.01)
+    xd = cf.kron_sum_solve_dense([ti.laplacian_1d(16)] * 4, ott.full(w.b))
+    xf = ott.full(x.numpy())
+    assert info["true_res"] <= 1e-6
+    assert np.linalg.norm(xf - xd) / np.linalg.norm(xd) <= 1e-5
+    # the library's residual agrees with the oracle's exact residual
+    res = osol.true_residual_norm(w.op, x.numpy(), w.b) / ott.norm(w.b)
+    assert abs(res - info["true_res"]) <= 1e-3 * res + 1e-14
+    assert info["iters"] <= 2 * w.params["maxit"]
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_convdiff_small_vs_dense(g, mode):
+    w = ti.workload("convdiff", d=4, n=12, maxit=60)
+    x, info = solve(g, w, mode, stop_safety=0.01)
+    M = ti.laplacian_1d(12) + 10 * ti.central_difference_1d(12)
+    xd = cf.kron_sum_solve_dense([M] * 4, ott.full(w.b))
+    err = np.linalg.norm(ott.full(x.numpy()) - xd) / np.linalg.norm(xd)
+    assert info["true_res"] <= 1e-6
+    assert err <= (1e-5 if mode == 0 else 1e-4)
+
+
+def test_convdiff_full_size_fp32(g):
+    # d=10, n=64, b random TT rank 4: the true residual reported by the
+    # library is re-computed exactly by the oracle in FP64
+    w = ti.workload("convdiff")
+    x, info = solve(g, w, g.MODE_FP32)
+    assert info["status"] == 0
+    res = osol.true_residual_norm(w.op, x.numpy(), w.b) / ott.norm(w.b)
+    assert res <= 1e-6
+    assert abs(res - info["true_res"]) <= 1e-2 * res
+    assert info["max_rank"] <= w.params["rmax"]
