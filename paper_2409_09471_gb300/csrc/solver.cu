@@ -35,8 +35,8 @@ double read_double(cudaStream_t st, const double* dev) {
 double inner_floor(int mode) {
   switch (mode) {
     case TT_MODE_FP64: return 0.0;
-    case TT_MODE_FP32: return 1e-5;
-    default: return 1e-3;
+    case TT_MODE_FP32: return 1e-7;
+    default: return 1e-4;
   }
 }
 
@@ -106,10 +106,30 @@ SolveResult sgmres_solve(const Ctx& c0, const TTop<double>& A64in, const TTv<dou
     gaussian_fill(S[k], f64, s * n[k], p.seed, 1024 + (uint64_t)k, std::pow((double)s, -0.5 / d),
                   c.st);
   }
+  // Gaussian TT-DRM drawn once per solve (Philox streams 2048 + k) at the
+  // capacity ranks; every rounding uses its leading sub-blocks
   DRMSource<T> drm;
   drm.seed = p.seed;
   drm.L[0] = drm.L[d] = 1;
   for (int k = 1; k < d; ++k) drm.L[k] = std::max(p.rmax, r_sol) + p.oversample;
+  std::vector<T*> drm_cores(d);
+  std::vector<double*> drm64_cores(d);
+  for (int k = 0; k < d; ++k) {
+    const int64_t cnt = drm.L[k] * n[k] * drm.L[k + 1];
+    const double sd = 1.0 / std::sqrt((double)cnt);
+    drm64_cores[k] = ar.take<double>(cnt);
+    gaussian_fill(drm64_cores[k], 1, cnt, p.seed, 2048 + (uint64_t)k, sd, c.st);
+    if (f64) {
+      drm_cores[k] = (T*)drm64_cores[k];
+    } else {
+      drm_cores[k] = ar.take<T>(cnt);
+      CopySeg sg;
+      sg.src = drm64_cores[k]; sg.dst = drm_cores[k]; sg.A = cnt; sg.sa = 1;
+      sg.src_f64 = 1; sg.dst_f64 = 0;
+      copy3d({sg}, c.st);
+    }
+  }
+  drm.core = (const T* const*)drm_cores.data();
 
   // ---- persistent buffers
   int64_t rb = 1;
@@ -141,6 +161,7 @@ SolveResult sgmres_solve(const Ctx& c0, const TTop<double>& A64in, const TTv<dou
   DRMSource<double> drm64;
   drm64.seed = drm.seed;
   for (int k = 0; k <= d; ++k) drm64.L[k] = drm.L[k];
+  drm64.core = (const double* const*)drm64_cores.data();
   double* Wm = ar.take<double>(s * p.maxit);
   double* Sr0 = ar.take<double>(s);
   double* ydev = ar.take<double>(p.maxit);
@@ -261,6 +282,10 @@ SolveResult sgmres_solve(const Ctx& c0, const TTop<double>& A64in, const TTv<dou
       kdone = k + 1;
       ++res.iters;
       if (hv[1] <= inner * betaS || hv[0] == 0.0) break;
+      // stagnation: less than 10% progress over the last 10 iterations ends the
+      // cycle (the restart continues from the true residual)
+      const size_t nh = res.res_hist.size();
+      if (kdone >= 20 && res.res_hist[nh - 1] > 0.9 * res.res_hist[nh - 11]) break;
     }
     // e = Round(sum_i y_i v_i)
     {
@@ -301,7 +326,7 @@ SolveResult sgmres_solve(const Ctx& c0, const TTop<double>& A64in, const TTv<dou
     terms[1].coef = -1.0;
     const double next_inner = std::max(std::min(0.5, p.stop_safety * p.tol / rel),
                                        inner_floor(c.mode));
-    tt_round_rand_dev<double>(c64, terms, std::max(0.1 * next_inner, 1e-14), p.rmax,
+    tt_round_rand_dev<double>(c64, terms, std::max(0.1 * next_inner, 1e-14), vcap_r,
                               p.oversample, drm64, r64);
     copy_tt(r64, rhs, nullptr, 0);
     cur_rhs = &rhs;

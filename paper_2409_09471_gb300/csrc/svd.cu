@@ -53,7 +53,10 @@ jacobi_kernel(const double* G, int l, int trans, double* GV, double* V, double* 
     if (lane == 0) s_tot = acc;
   }
   __syncthreads();
-  const double tiny = s_tot * (double)eps_t * (double)eps_t * (double)eps_t * (double)eps_t;
+  // thresholds in the kernel's own precision (FP64 math is slow on this part)
+  const T tot_t = (T)s_tot;
+  const T tiny = (T)(s_tot * (double)eps_t * (double)eps_t * (double)eps_t * (double)eps_t);
+  const T abs_thr = tol * eps_t * tot_t;
   const int lp = l + (l & 1);   // even number of players (index l is a dummy when l is odd)
   int sweep = 0;
   for (; sweep < MAX_SWEEPS; ++sweep) {
@@ -77,9 +80,8 @@ jacobi_kernel(const double* G, int l, int trans, double* GV, double* V, double* 
         // converged pair: relative test, or an inner product at the rounding
         // level of the whole matrix (columns at noise level cannot be made
         // relatively orthogonal in this precision)
-        if (ga == T(0) || (double)al <= tiny || (double)be <= tiny ||
-            fabs((double)ga) <= (double)tol * sqrt((double)al * (double)be) ||
-            fabs((double)ga) <= (double)tol * (double)eps_t * s_tot)
+        if (ga == T(0) || al <= tiny || be <= tiny || fabs(ga) <= tol * sqrt(al) * sqrt(be) ||
+            fabs(ga) <= abs_thr)
           continue;
         const T zeta = (be - al) / (T(2) * ga);
         const T t = (zeta >= T(0) ? T(1) : T(-1)) / (fabs(zeta) + sqrt(T(1) + zeta * zeta));
