@@ -121,6 +121,25 @@ int tt_dot(int mode, const tt_vec* x, const tt_vec* y, double* out,
 size_t tt_dot_workspace(int mode, const tt_vec* x, const tt_vec* y);
 
 /*
+ * tt_dot_noalloc - the inner product of tt_dot for callers that cannot
+ * allocate device memory: for example code that runs while a memory manager
+ * owns all device memory, or inside a host program that must not call
+ * cudaMalloc once it is running.  The paper has no counterpart; this is an
+ * interface convenience.  No workspace is passed: the Gram sweep uses a fixed
+ * TT_NOALLOC_SCRATCH_BYTES device array inside the library, which every GPU
+ * that loads the library keeps until the process exits.  Inputs that would
+ * need more scratch than that are rejected with TT_ERR_ARG before any device
+ * work.  The first call on a device looks up the array's device address; make
+ * that first call before any stream capture.  All calls share the one array, so
+ * calls that overlap on the GPU (different streams, or threads, at the same
+ * time) race; serialise them.  The function calls no cudaMalloc or cudaFree.
+ * out (device, double[1]); x, y as for tt_dot.
+ */
+#define TT_NOALLOC_SCRATCH_BYTES (16u << 20)
+#define TT_MAX_DEVICES 64
+int tt_dot_noalloc(int mode, const tt_vec* x, const tt_vec* y, double* out, void* stream);
+
+/*
  * tt_round_rand - randomize-then-orthogonalize rounding (Sec. 3.3) of the
  * implicit sum  sum_b coef[b] * X_b  (nterms >= 1 TT vectors with equal mode
  * sizes), without forming the block cores:

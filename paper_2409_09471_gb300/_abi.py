@@ -69,6 +69,7 @@ def _load():
         "tt_sketch_workspace": (sz, [cint, P(TTVec), i64]),
         "tt_dot": (cint, [cint, P(TTVec), P(TTVec), V, V, sz, V]),
         "tt_dot_workspace": (sz, [cint, P(TTVec), P(TTVec)]),
+        "tt_dot_noalloc": (cint, [cint, P(TTVec), P(TTVec), V, V]),
         "tt_round_rand": (cint, [cint, cint, P(TTVec), P(dbl), dbl, i64, i64, u64, c_vpp, c_i64p,
                                  P(TTVecOut), V, sz, V]),
         "tt_round_rand_workspace": (sz, [cint, cint, P(TTVec), i64, i64]),

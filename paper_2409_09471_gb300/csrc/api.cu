@@ -157,13 +157,13 @@ void do_matvec(int mode, const tt_op* A, const tt_vec* x, const tt_vec* y, void*
 }
 
 template <typename F>
-size_t measure(F&& f) {
+size_t measure(F&& f, bool margin = true) {
   DryGuard g;
   try {
     f();
   } catch (size_t peak) {
     // margin for allocations whose size the dry run bounds from below
-    return peak + peak / 32 + (16u << 20);
+    return margin ? peak + peak / 32 + (16u << 20) : peak;
   } catch (const Error& e) {
     g_last_error = e.what();
     return 0;
@@ -223,13 +223,13 @@ void do_sketch(int mode, const tt_vec* x, int64_t s, void* const* S, double* out
 
 template <typename T>
 void do_dot(int mode, const tt_vec* x, const tt_vec* y, double* out, void* ws, size_t bytes,
-            void* stream, bool dry) {
+            void* stream, bool dry, bool with_gemm = true) {
   TTv<T> xv = view<T>(x, "x");
   TTv<T> yv = view<T>(y, "y");
   if (xv.d != yv.d) throw Error(TT_ERR_ARG, "dot: d mismatch");
   same_modes(xv.n, yv.n, xv.d, "dot");
   if (!dry && !out) throw Error(TT_ERR_ARG, "dot: null out");
-  Carved cv = carve(mode, ws, bytes, stream, dry);
+  Carved cv = carve(mode, ws, bytes, stream, dry, with_gemm);
   fix_ctx(cv);
   tt_dot_dev<T>(cv.ctx, xv, yv, out);
   if (dry) throw (size_t)cv.ar.peak;
@@ -320,6 +320,29 @@ int tt_dot(int mode, const tt_vec* x, const tt_vec* y, double* out, void* ws, si
     else do_dot<float>(mode, x, y, out, ws, ws_bytes, stream, false);
   });
 }
+
+namespace ttsg {
+// Inner product without split-K scratch, on a caller-chosen workspace; used by
+// the allocation-free entry point (noalloc.cu).
+size_t dot_bytes_without_splitk(int mode, const tt_vec* x, const tt_vec* y) {
+  return measure([&] {
+    check_mode(mode);
+    if (mode == TT_MODE_FP64)
+      do_dot<double>(mode, x, y, nullptr, nullptr, 0, nullptr, true, false);
+    else
+      do_dot<float>(mode, x, y, nullptr, nullptr, 0, nullptr, true, false);
+  }, false);
+}
+int dot_on_workspace_without_splitk(int mode, const tt_vec* x, const tt_vec* y, double* out,
+                                    void* ws, size_t bytes, void* stream) {
+  return guarded([&] {
+    check_mode(mode);
+    if (mode == TT_MODE_FP64) do_dot<double>(mode, x, y, out, ws, bytes, stream, false, false);
+    else do_dot<float>(mode, x, y, out, ws, bytes, stream, false, false);
+  });
+}
+void set_last_error(const std::string& m) { g_last_error = m; }
+}  // namespace ttsg
 
 size_t tt_round_rand_workspace(int mode, int nterms, const tt_vec* terms, int64_t rmax,
                                int64_t oversample) {
