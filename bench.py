@@ -58,6 +58,9 @@ def parse():
     ap.add_argument("--no-fp64-leg", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=20.0,
                     help="budget of the host oracle sample")
+    ap.add_argument("--case", choices=["solve", "round"], default="solve",
+                    help="'round': time one randomized rounding of w - h v at the workload's "
+                         "sizes (the kernel-level case used for ncu captures)")
     return ap.parse_args()
 
 
@@ -233,12 +236,13 @@ def run_ours(args):
     info = None
     for i in range(args.warmup):
         if i == args.warmup - 1:
-            lib.tt_profile(0x1F)
+            lib.tt_profile(0x7F)
         x, info = g.tt_sgmres_solve(op, b, mode=mode, workspace=ws, **kw)
         if ws is None:
             ws = torch.empty(info["workspace_bytes"], dtype=torch.uint8, device="cuda")
     torch.cuda.synchronize()
-    classes = {0: "gemm", 1: "qr_f64", 2: "jacobi_svd", 3: "lstsq", 4: "misc"}
+    classes = {0: "gemm", 1: "qr_f64", 2: "jacobi_svd", 3: "lstsq", 4: "misc", 5: "gram_f64",
+               6: "chol_f64"}
     prof = {}
     for cl in classes:
         ms, nl, fl, by = ctypes.c_double(), ctypes.c_int64(), ctypes.c_double(), ctypes.c_double()
@@ -363,6 +367,7 @@ def run_ours(args):
             "config": {"workload": WORKLOAD, "mode": mode_name, "parallelism": "replicas",
                        "l2": "flushed (512 MiB write) before every step"},
             "iters_per_solve": statistics.median(iters), "true_res": info["true_res"],
+            "svd_nonconverged": info.get("svd_nonconverged"),
             "cycles": info["cycles"], "max_rank": info["max_rank"],
             "gpu_launches": int(launches), "roofline": roof,
             "kernel_time_ms_by_class_warmup": {k: round(v["ms"], 3) for k, v in prof.items()},
@@ -385,8 +390,37 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_round_case(args):
+    """One Gram-Schmidt rounding of the solver at the workload's sizes:
+    ``Round(A v - h v)`` with v a random rank-64 TT (d=10, n=64), rank cap 64,
+    oversampling 10, tolerance 1e-7, in the selected mode."""
+    import torch
+    import paper_2409_09471_gb300 as g
+    mode_name = args.mode or "fp32"
+    mode = {"tf32": g.MODE_TF32, "fp32": g.MODE_FP32, "fp64": g.MODE_FP64}[mode_name]
+    w, p = workload()
+    dt = g.mode_dtype(mode)
+    v = g.TT.from_numpy(ti.random_tt(w.ns, [1] + [64] * (w.d - 1) + [1], seed=5), dt)
+    Av = g.tt_matvec(g.op_to_device(w.op, dt), v, mode=mode)
+    times = []
+    for i in range(args.warmup + args.steps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        y = g.tt_round_rand([Av, v], [1.0, -0.3], 1e-7, 64, 10, seed=1, mode=mode)
+        e1.record()
+        torch.cuda.synchronize()
+        if i >= args.warmup:
+            times.append(e0.elapsed_time(e1))
+    print(json.dumps({"case": "round", "mode": mode_name, "ms_per_call": statistics.median(times),
+                      "out_ranks": y.ranks}), flush=True)
+
+
 def main():
     args = parse()
+    if args.case == "round":
+        run_round_case(args)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:

@@ -148,9 +148,13 @@ int tt_dot_noalloc(int mode, const tt_vec* x, const tt_vec* y, double* out, void
  *   2. right partial contractions of every term with a Gaussian TT-DRM;
  *   3. left-to-right sweep: Y = Z W, FP64 Householder QR of Y, core <- Q,
  *      M = Q^T Z carried into the next core;
- *   4. right-to-left truncation: FP64 Householder QR of the core unfolding and
- *      a small Jacobi SVD; per-bond threshold eps ||T|| / sqrt(d-1), ranks
- *      capped at rmax.  Cores 2..d of the result are right-orthogonal.
+ *   4. truncation to the tolerance eps ||T|| and ranks <= rmax.  TT_MODE_FP64:
+ *      right-to-left TT-SVD sweep (FP64 Householder QR of each core unfolding
+ *      and a small Jacobi SVD, per-bond threshold eps ||T|| / sqrt(d-1)); cores
+ *      2..d of the result are right-orthogonal.  Float modes: every bond is cut
+ *      from the same left-orthogonal tensor (eigenvectors of its right Gram
+ *      matrices, FP64 Cholesky + Jacobi, all bonds in one launch, threshold
+ *      eps ||T|| / (d-1)); the result is not orthogonalised.
  * coef: host array [nterms].  drm: NULL to draw the TT-DRM from the Philox
  * stream (seed, streams 2048 + k) with capacity ranks rmax + oversample, or a
  * host array of d device pointers to DRM cores [L_{k-1}][n_k][L_k] with ranks
@@ -244,10 +248,11 @@ size_t tt_sgmres_solve_workspace(const tt_op* A, const tt_vec* b, const tt_solve
 
 /*
  * Measurement support (no counterpart in the method): tt_profile(mask) clears
- * the launch records and, for every class bit set in mask (1 GEMM, 2 FP64 QR,
- * 4 Jacobi SVD, 8 least squares, 16 copies / generators), brackets each later
- * launch of that class with CUDA events on its stream.  tt_profile_read
- * synchronises those events and returns, for one class index (0..4), the summed
+ * the launch records and, for every class bit set in mask (1 GEMM, 2 FP64
+ * Householder QR, 4 Jacobi SVD, 8 least squares, 16 copies / generators, 32 FP64
+ * Gram, 64 FP64 Cholesky), brackets each later launch of that class with CUDA
+ * events on its stream.  tt_profile_read synchronises those events and
+ * returns, for one class index (0..6), the summed
  * event time in milliseconds, the number of launches and their algorithmic
  * FLOPs and bytes (host outputs, any may be NULL).  tt_profile(0) disables it.
  */

@@ -85,7 +85,37 @@ def right_partial_contractions(X, drm):
     return W
 
 
-def rto_round(terms, drm, eps=0.0, rmax=None, oversample=10):
+def truncate_simultaneous(cores, eps=0.0, rmax=None):
+    """Truncation of a left-orthogonal TT (cores 1..d-1 left-orthogonal) with
+    all bonds decided from the same tensor: the right Gram matrices
+    ``G_mu = C_{>mu}^T C_{>mu}`` (one right-to-left sweep) have the squared
+    bond singular values as eigenvalues; bond mu keeps the eigenvectors
+    ``W_mu`` of the largest ones (smallest rank with tail <= eps ||T|| /
+    (d - 1), capped at rmax) and core mu becomes ``W_{mu-1}^T C_mu W_mu``.
+    Telescoping over the bonds bounds the error by the sum of the dropped
+    tails, hence by ``eps ||T||``."""
+    d = len(cores)
+    G = [None] * (d + 1)
+    G[d] = np.ones((1, 1))
+    for mu in range(d, 1, -1):
+        C = cores[mu - 1]
+        acc = np.zeros((C.shape[0], C.shape[0]))
+        for i in range(C.shape[1]):
+            acc += C[:, i, :] @ G[mu] @ C[:, i, :].T
+        G[mu - 1] = acc
+    nrm = np.sqrt(max(np.trace(G[1]), 0.0))
+    delta = eps * nrm / max(d - 1, 1)
+    W = [np.ones((1, 1))] + [None] * (d - 1) + [np.ones((1, 1))]
+    for mu in range(1, d):
+        lam, V = np.linalg.eigh(G[mu])
+        order = np.argsort(lam)[::-1]
+        sig = np.sqrt(np.maximum(lam[order], 0.0))
+        r = truncation_rank(sig, delta, rmax)
+        W[mu] = V[:, order[:r]]
+    return [np.einsum("ap,aib,bq->piq", W[k], cores[k], W[k + 1]) for k in range(d)]
+
+
+def rto_round(terms, drm, eps=0.0, rmax=None, oversample=10, truncation="sequential"):
     """Randomize-then-orthogonalize rounding of ``sum_b a_b X^(b)``.
 
     ``terms`` is a list of ``(a_b, cores_b)``; ``drm`` is a Gaussian TT-DRM
@@ -100,7 +130,8 @@ def rto_round(terms, drm, eps=0.0, rmax=None, oversample=10):
        X^(b)_{mu+1}``; the last core is ``sum_b Z^(b)_d``.
     3. Right-to-left truncated SVDs with ``delta = eps ||T|| / sqrt(d-1)``
        and ranks capped at ``rmax`` (this sweep leaves cores 2..d
-       right-orthogonal, so ``||T||`` equals ``||core_1||``).
+       right-orthogonal, so ``||T||`` equals ``||core_1||``); or, with
+       ``truncation="simultaneous"``, :func:`truncate_simultaneous`.
     """
     d = len(terms[0][1])
     ns = [c.shape[1] for c in terms[0][1]]
@@ -119,6 +150,10 @@ def rto_round(terms, drm, eps=0.0, rmax=None, oversample=10):
         Mb = [Q.T @ Zb.reshape(rows, Zb.shape[2]) for Zb in Z]
         Z = [np.einsum("qp,pic->qic", M, X[mu]) for M, (_, X) in zip(Mb, terms)]
     out.append(sum(Z))
+    if truncation == "simultaneous":
+        trunc = eps > 0.0 or any(c.shape[2] > (rmax if rmax is not None else 1 << 60)
+                                 for c in out[:-1])
+        return truncate_simultaneous(out, eps, rmax) if trunc else out
     # 3. truncation sweep
     nrm = np.linalg.norm(out[-1])
     delta = eps * nrm / np.sqrt(d - 1)

@@ -45,6 +45,20 @@ void qr_f64(const void* Y, int y_f64, int64_t m, int64_t l, int64_t sr, int64_t 
             int q_f64, int64_t ldq, double* R, void* ws, size_t ws_bytes, int* err_flag,
             cudaStream_t st);
 
+// ----------------------------------------------------- Gram / Cholesky (chol.cu)
+// G (l x l, double, full symmetric) = Y^T Y in FP64 for Y (m x l, element
+// (i,j) at Y[i*sr + j*sc], float or double).
+size_t gram_workspace(int64_t m, int64_t l);
+void gram_f64(const void* Y, int y_f64, int64_t m, int64_t l, int64_t sr, int64_t sc, double* G,
+              void* ws, size_t ws_bytes, cudaStream_t st);
+// G + rel_shift * trace(G) * I = R^T R with R upper triangular (row-major,
+// double); clamped non-positive pivots increment *err_flag.
+void chol_f64(const double* G, int64_t l, double rel_shift, double* R, int* err_flag,
+              cudaStream_t st);
+// Batched form: problem i factors G[i] (l[i] x l[i]) into R[i], one CTA each.
+void chol_f64_batched(int count, const double* const* G, const int64_t* l, double rel_shift,
+                      double* const* R, int* err_flag, cudaStream_t st);
+
 // ------------------------------------------------------------ SVD (svd.cu)
 // One-sided Jacobi on the columns of G (l x l, row-major double input, or its
 // transpose when ``trans``):
@@ -58,6 +72,25 @@ void qr_f64(const void* Y, int y_f64, int64_t m, int64_t l, int64_t sr, int64_t 
 void jacobi_svd(const double* G, int64_t l, int trans, int f32, double* GV, double* V, double* sigma,
                 double eps, int64_t dm1, int64_t rmax, const double* norm_in, double* norm_out,
                 int* rank_out, int* err_flag, cudaStream_t st);
+
+// Batched form: one CTA per problem; every problem uses the same rank rule
+// parameters.  With norm_in == nullptr each problem takes its own sqrt(sum
+// sigma^2) as ||T||; norm_out (if set) receives problem 0's norm.
+struct JacobiBatchArgs {
+  int count = 0, trans = 0, f32 = 1;
+  double eps = 0.0;
+  int64_t dm1 = 1, rmax = 1;
+  const double* norm_in = nullptr;
+  double* norm_out = nullptr;
+  int* err = nullptr;
+  const double* G[TT_MAX_D] = {};
+  int64_t l[TT_MAX_D] = {};
+  double* GV[TT_MAX_D] = {};
+  double* V[TT_MAX_D] = {};
+  double* sigma[TT_MAX_D] = {};
+  int* rank_out[TT_MAX_D] = {};
+};
+void jacobi_svd_batched(const JacobiBatchArgs& a, cudaStream_t st);
 
 // ---------------------------------------------------------- LS (lstsq.cu)
 size_t lstsq_workspace(int64_t s, int64_t kmax);

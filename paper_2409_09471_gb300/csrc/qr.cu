@@ -35,6 +35,7 @@ namespace {
 
 constexpr int QR_THREADS = 256;
 constexpr int QB = 8;                        // reflectors per Q-formation block
+constexpr int NREP = 8;                      // replicas of every reduction slot
 constexpr long long SPIN_LIMIT = 1ll << 24;  // bounded spin (well under a second)
 
 struct QRArgs {
@@ -62,36 +63,37 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
-// Returns false when the barrier timed out (bit 0 of the error flag is then set).
-__device__ bool grid_barrier(unsigned* bar, int* err) {
+// Grid barrier on a monotonic arrival counter (bar[0], zeroed before the
+// launch): barrier number b completes when the counter reaches (b + 1) * P, so
+// each CTA keeps a running target and needs one release fence, one atomic and
+// a poll of the same word; no reset, no second word.  Returns false when the
+// barrier timed out (bit 0 of the error flag is then set).
+__device__ bool grid_barrier(unsigned* bar, unsigned& target, int* err) {
   __shared__ int fail;
   __syncthreads();
   if (threadIdx.x == 0) {
     fail = 0;
-    volatile unsigned* vgen = bar + 1;
-    const unsigned gen = *vgen;
+    target += gridDim.x;
     __threadfence();
-    const unsigned arrived = atomicAdd(bar, 1u);
-    if (arrived == gridDim.x - 1) {
-      atomicExch(bar, 0u);
-      __threadfence();
-      atomicAdd(bar + 1, 1u);
-    } else {
-      long long spins = 0;
-      while (*vgen == gen) {
-        if (++spins > SPIN_LIMIT || (*(volatile int*)err & 1)) {
-          atomicOr(err, 1);
-          fail = 1;
-          break;
-        }
-        __nanosleep(32);
+    atomicAdd(bar, 1u);
+    volatile unsigned* vc = bar;
+    long long spins = 0;
+    while ((int)(*vc - target) < 0) {
+      if (++spins > SPIN_LIMIT || (*(volatile int*)err & 1)) {
+        atomicOr(err, 1);
+        fail = 1;
+        break;
       }
+      __nanosleep(20);
     }
     __threadfence();
   }
   __syncthreads();
   return fail == 0;
 }
+
+__device__ __forceinline__ int64_t imin64(int64_t a, int64_t b) { return a < b ? a : b; }
+__device__ __forceinline__ int64_t imax64(int64_t a, int64_t b) { return a > b ? a : b; }
 
 // Block-wide sum; every thread gets the result.
 __device__ double block_sum(double v, double* red) {
@@ -115,10 +117,12 @@ __global__ void __launch_bounds__(QR_THREADS) qr_coop_kernel(const QRArgs a) {
   double* tau = wv + L4;                         // [l]
   double* Tb = tau + l;                          // [QB][QB]
   double* Wb = Tb + QB * QB;                     // [QB][l]
+  double* Vb = Wb + QB * l;                      // [QB][rows]
   __shared__ double red[QR_THREADS / 32];
   __shared__ double sc[8];
 
   const int c = blockIdx.x;
+  unsigned btarget = 0;  // running grid-barrier target (used by thread 0)
   const int64_t r0 = (int64_t)c * a.rows;
   const int64_t r1 = a.m < r0 + a.rows ? a.m : r0 + a.rows;
   const int nloc = r1 > r0 ? (int)(r1 - r0) : 0;
@@ -146,7 +150,7 @@ __global__ void __launch_bounds__(QR_THREADS) qr_coop_kernel(const QRArgs a) {
       if (s != 0.0) atomicAdd(a.nrm, s);
       if (r0 == 0 && nloc > 0) a.pub[0] = Yl[0];
     }
-    if (!grid_barrier(a.bar, a.err)) return;
+    if (!grid_barrier(a.bar, btarget, a.err)) return;
     if (tid == 0) { sc[0] = __ldcg(a.nrm); sc[1] = __ldcg(a.pub); }
     __syncthreads();
   }
@@ -168,29 +172,32 @@ __global__ void __launch_bounds__(QR_THREADS) qr_coop_kernel(const QRArgs a) {
     if (tid == 0) tau[j] = t;
     __syncthreads();
     if (j + 1 >= l) break;
-    double* slot = a.acc + (size_t)j * L4;
+    double* slot = a.acc + ((size_t)(c % NREP) * l + j) * L4;  // this CTA's replica
+    // local rows holding v_j: the diagonal row (v = 1) and the rows below it
+    const int64_t jl = (int64_t)j - r0;
+    const int ldiag = (jl >= 0 && jl < nloc) ? (int)jl : -1;
+    const int lbeg = jl + 1 > 0 ? (int)imin64(jl + 1, nloc) : 0;
     // partial products w[col] = sum_{i >= j} v_i Y[i, col], one thread per column
     for (int col = j + 1 + tid; col < l; col += QR_THREADS) {
-      double p = 0.0;
-      for (int li = 0; li < nloc; ++li) p += vval(li, j) * Yl[li * ldy + col];
-      if (p != 0.0) atomicAdd(slot + col, p);
+      double p = ldiag >= 0 ? Yl[ldiag * ldy + col] : 0.0;
+      for (int li = lbeg; li < nloc; ++li) p = fma(Yl[li * ldy + j], Yl[li * ldy + col], p);
+      atomicAdd(slot + col, p);
     }
     // S1, S2, S3 of column j+1 over rows > j+1 (before the update)
     {
       double s1 = 0.0, s2 = 0.0, s3 = 0.0;
-      for (int li = tid; li < nloc; li += QR_THREADS) {
-        if (r0 + li > j + 1) {
-          const double y = Yl[li * ldy + j + 1], v = Yl[li * ldy + j];
-          s1 += y * y; s2 += v * y; s3 += v * v;
-        }
+      const int lb2 = jl + 2 > 0 ? (int)imin64(jl + 2, nloc) : 0;
+      for (int li = lb2 + tid; li < nloc; li += QR_THREADS) {
+        const double y = Yl[li * ldy + j + 1], v = Yl[li * ldy + j];
+        s1 = fma(y, y, s1); s2 = fma(v, y, s2); s3 = fma(v, v, s3);
       }
       s1 = block_sum(s1, red);
       s2 = block_sum(s2, red);
       s3 = block_sum(s3, red);
       if (tid == 0) {
-        if (s1 != 0.0) atomicAdd(slot + l, s1);
-        if (s2 != 0.0) atomicAdd(slot + l + 1, s2);
-        if (s3 != 0.0) atomicAdd(slot + l + 2, s3);
+        atomicAdd(slot + l, s1);
+        atomicAdd(slot + l + 1, s2);
+        atomicAdd(slot + l + 2, s3);
         const int64_t o = j + 1 - r0;
         if (o >= 0 && o < nloc) {
           a.pub[2 * (j + 1)] = Yl[o * ldy + j + 1];
@@ -198,28 +205,44 @@ __global__ void __launch_bounds__(QR_THREADS) qr_coop_kernel(const QRArgs a) {
         }
       }
     }
-    if (!grid_barrier(a.bar, a.err)) return;
-    for (int col = j + 1 + tid; col < L4; col += QR_THREADS) wv[col] = __ldcg(slot + col);
+    if (!grid_barrier(a.bar, btarget, a.err)) return;
+    for (int col = j + 1 + tid; col < L4; col += QR_THREADS) {
+      double v = 0.0;
+#pragma unroll
+      for (int q = 0; q < NREP; ++q) v += __ldcg(a.acc + ((size_t)q * l + j) * L4 + col);
+      wv[col] = v;
+    }
     if (tid == 0) { sc[2] = __ldcg(a.pub + 2 * (j + 1)); sc[3] = __ldcg(a.pub + 2 * (j + 1) + 1); }
     __syncthreads();
-    const int ncols = l - j - 1;
-    for (int e = tid; e < nloc * ncols; e += QR_THREADS) {
-      const int li = e / ncols, col = j + 1 + e % ncols;
-      const double v = vval(li, j);
-      if (v != 0.0) Yl[li * ldy + col] -= t * v * wv[col];
+    // update rows >= j: Y[i, col] -= (tau v_i) w[col]
+    for (int col = j + 1 + tid; col < l; col += QR_THREADS) wv[col] *= -t;
+    __syncthreads();
+    {
+      const int ncols = l - j - 1;
+      const int r_lo = ldiag >= 0 ? ldiag : lbeg;
+      const int nr = nloc - r_lo;
+      for (int e = tid; e < nr * ncols; e += QR_THREADS) {
+        const int li = r_lo + e / ncols, col = j + 1 + e % ncols;
+        const double v = li == ldiag ? 1.0 : Yl[li * ldy + j];
+        Yl[li * ldy + col] = fma(v, wv[col], Yl[li * ldy + col]);
+      }
     }
-    const double wn = wv[j + 1], S1 = wv[l], S2 = wv[l + 1], S3 = wv[l + 2];
-    alpha = sc[2] - t * sc[3] * wn;
-    sigma2 = S1 - 2.0 * t * wn * S2 + t * t * wn * wn * S3;
+    // wv[j+1] now holds -tau w[j+1]
+    const double mtw = wv[j + 1], S1 = wv[l], S2 = wv[l + 1], S3 = wv[l + 2];
+    alpha = sc[2] + sc[3] * mtw;
+    sigma2 = S1 + 2.0 * mtw * S2 + mtw * mtw * S3;
     __syncthreads();
     if (!(sigma2 >= 0.01 * S1)) {
       // possible cancellation: recompute the norm of the updated column exactly
       double s = 0.0;
-      for (int li = tid; li < nloc; li += QR_THREADS)
-        if (r0 + li > j + 1) { const double v = Yl[li * ldy + j + 1]; s += v * v; }
+      const int lb2 = jl + 2 > 0 ? (int)imin64(jl + 2, nloc) : 0;
+      for (int li = lb2 + tid; li < nloc; li += QR_THREADS) {
+        const double v = Yl[li * ldy + j + 1];
+        s = fma(v, v, s);
+      }
       s = block_sum(s, red);
-      if (tid == 0 && s != 0.0) atomicAdd(a.nrm + j + 1, s);
-      if (!grid_barrier(a.bar, a.err)) return;
+      if (tid == 0) atomicAdd(a.nrm + j + 1, s);
+      if (!grid_barrier(a.bar, btarget, a.err)) return;
       if (tid == 0) sc[4] = __ldcg(a.nrm + j + 1);
       __syncthreads();
       sigma2 = sc[4];
@@ -251,7 +274,7 @@ __global__ void __launch_bounds__(QR_THREADS) qr_coop_kernel(const QRArgs a) {
     const int li = e / l, col = e % l;
     Ql[li * ldy + col] = (r0 + li == col) ? 1.0 : 0.0;
   }
-  if (!grid_barrier(a.bar, a.err)) return;
+  if (!grid_barrier(a.bar, btarget, a.err)) return;
   for (int bi = nblk - 1; bi >= 0; --bi) {
     const int j0 = bi * QB, kb = min(QB, l - j0);
     if (tid == 0) {
@@ -268,17 +291,33 @@ __global__ void __launch_bounds__(QR_THREADS) qr_coop_kernel(const QRArgs a) {
         for (int r = i + 1; r < QB; ++r) Tb[r * QB + i] = 0.0;
       }
     }
+    // stage v of the block's reflectors (unit diagonal, zeros above) in Vb
+    for (int e = tid; e < QB * nloc; e += QR_THREADS) {
+      const int r = e / nloc, li = e % nloc;
+      Vb[e] = r < kb ? vval(li, j0 + r) : 0.0;
+    }
+    __syncthreads();
     // W = V_b^T Q over the local rows, columns j0..l-1
-    double* slot = a.accq + (size_t)bi * QB * l;
+    const int nblk_all = (l + QB - 1) / QB;
+    double* slot = a.accq + ((size_t)(c % NREP) * nblk_all + bi) * QB * l;
     const int ncols = l - j0;
+    const int vlo = (int)imax64(0, imin64((int64_t)j0 - r0, nloc));
     for (int e = tid; e < kb * ncols; e += QR_THREADS) {
       const int r = e / ncols, col = j0 + e % ncols;
       double s = 0.0;
-      for (int li = 0; li < nloc; ++li) s += vval(li, j0 + r) * Ql[li * ldy + col];
-      if (s != 0.0) atomicAdd(slot + (size_t)r * l + col, s);
+      for (int li = vlo; li < nloc; ++li) s = fma(Vb[r * nloc + li], Ql[li * ldy + col], s);
+      atomicAdd(slot + (size_t)r * l + col, s);
     }
-    if (!grid_barrier(a.bar, a.err)) return;
-    for (int e = tid; e < kb * l; e += QR_THREADS) Wb[e] = __ldcg(slot + e);
+    if (!grid_barrier(a.bar, btarget, a.err)) return;
+    for (int e = tid; e < QB * l; e += QR_THREADS) {
+      double v = 0.0;
+      if (e < kb * l) {
+#pragma unroll
+        for (int q = 0; q < NREP; ++q)
+          v += __ldcg(a.accq + ((size_t)q * nblk_all + bi) * QB * l + e);
+      }
+      Wb[e] = v;
+    }
     __syncthreads();
     // Wb <- T Wb
     for (int col = j0 + tid; col < l; col += QR_THREADS) {
@@ -295,11 +334,12 @@ __global__ void __launch_bounds__(QR_THREADS) qr_coop_kernel(const QRArgs a) {
     }
     __syncthreads();
     // Q -= V_b (T W)
-    for (int e = tid; e < nloc * ncols; e += QR_THREADS) {
-      const int li = e / ncols, col = j0 + e % ncols;
-      double s = 0.0;
-      for (int r = 0; r < kb; ++r) s += vval(li, j0 + r) * Wb[r * l + col];
-      Ql[li * ldy + col] -= s;
+    for (int e = tid; e < (nloc - vlo) * ncols; e += QR_THREADS) {
+      const int li = vlo + e / ncols, col = j0 + e % ncols;
+      double s = Ql[li * ldy + col];
+#pragma unroll
+      for (int r = 0; r < QB; ++r) s = fma(-Vb[r * nloc + li], Wb[r * l + col], s);
+      Ql[li * ldy + col] = s;
     }
     __syncthreads();
   }
@@ -335,14 +375,14 @@ QRPlan plan(int64_t m, int64_t l, int sms, bool want_q) {
   p.rows = (int)ceil_div(m, P);
   p.P = (int)ceil_div(m, p.rows);
   p.ldy = (int)l + 1;
-  p.smem = ((size_t)p.rows * p.ldy * (want_q ? 2 : 1) + (l + 4) + l + QB * QB + QB * l) *
-           sizeof(double);
+  p.smem = ((size_t)p.rows * p.ldy * (want_q ? 2 : 1) + (l + 4) + l + QB * QB + QB * l +
+            (size_t)QB * p.rows) * sizeof(double);
   return p;
 }
 
 size_t slots_doubles(int64_t l) {
   const int64_t nblk = (l + QB - 1) / QB;
-  return (size_t)(l * (l + 4) + l + 2 * (l + 1) + nblk * QB * QB + nblk * QB * l);
+  return (size_t)(NREP * l * (l + 4) + l + 2 * (l + 1) + nblk * QB * QB + NREP * nblk * QB * l);
 }
 
 }  // namespace
@@ -370,12 +410,12 @@ void qr_f64(const void* Y, int y_f64, int64_t m, int64_t l, int64_t sr, int64_t 
   a.Q = Q; a.q_f64 = q_f64; a.ldq = ldq; a.R = R;
   const int64_t nblk = (l + QB - 1) / QB;
   a.acc = slots;
-  a.nrm = a.acc + l * (l + 4);
+  a.nrm = a.acc + NREP * l * (l + 4);
   a.pub = a.nrm + l;
   a.vtv = a.pub + 2 * (l + 1);
   a.accq = a.vtv + nblk * QB * QB;
   a.bar = bar; a.err = err_flag; a.rows = p.rows; a.ldy = p.ldy;
-  TT_CUDA(cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned), st));
+  TT_CUDA(cudaMemsetAsync(bar, 0, 64 * sizeof(unsigned), st));
   TT_CUDA(cudaMemsetAsync(slots, 0, sizeof(double) * slots_doubles(l), st));
   static bool attr = false;
   if (!attr) {

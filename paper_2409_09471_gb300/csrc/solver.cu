@@ -260,8 +260,10 @@ SolveResult sgmres_solve(const Ctx& c0, const TTop<double>& A64in, const TTv<dou
       terms[1].coef = -1.0;
       terms[1].coef_dev = scal + 1;
       tt_round_rand_dev<T>(c, terms, round_tol, p.rmax, p.oversample, drm, V[k + 1]);
-      // h_{k+1,k} = ||v~|| = ||core 1|| (cores 2..d are right-orthogonal)
-      sumsq(V[k + 1].core[0], f64, V[k + 1].core_elems(0), scal + 2, c.scratch + 16, c.st);
+      // h_{k+1,k} = ||v~||: the norm of core 1 when cores 2..d are
+      // right-orthogonal (FP64 mode), otherwise the Gram sweep
+      if (f64) sumsq(V[k + 1].core[0], f64, V[k + 1].core_elems(0), scal + 2, c.scratch + 16, c.st);
+      else tt_dot_dev<T>(c, V[k + 1], V[k + 1], scal + 2);
       sqrt_scalar(scal + 2, scal + 3, c.st);
       {
         CopySeg sg;

@@ -16,6 +16,7 @@ namespace ttsg {
 namespace {
 
 constexpr int SVD_THREADS = 1024;
+constexpr int MAX_SVD_BATCH = TT_MAX_D;
 constexpr int MAX_SWEEPS = 60;
 
 template <typename T>
@@ -25,18 +26,55 @@ __device__ __forceinline__ T warp_sum_t(T v) {
   return v;
 }
 
+struct JacobiBatch {
+  int count;
+  int trans, f32;
+  double eps;
+  long long dm1, rmax;
+  const double* norm_in;   // shared input norm (nullptr: each problem's own)
+  double* norm_out;        // written by problem 0 when set
+  const double* G[MAX_SVD_BATCH];
+  int l[MAX_SVD_BATCH];
+  double* GV[MAX_SVD_BATCH];
+  double* V[MAX_SVD_BATCH];
+  double* sigma[MAX_SVD_BATCH];
+  int* rank_out[MAX_SVD_BATCH];
+};
+
+template <typename T>
+__device__ __forceinline__ T group_sum8(T v) {
+  // sum over the 8 lanes of a lane group (xor offsets 4, 2, 1)
+  v += __shfl_xor_sync(0xffffffffu, v, 4);
+  v += __shfl_xor_sync(0xffffffffu, v, 2);
+  v += __shfl_xor_sync(0xffffffffu, v, 1);
+  return v;
+}
+
+// One pair of columns per group of 8 lanes (4 pairs per warp): fewer shuffle
+// levels and a smaller block make each parallel step short.
 template <typename T>
 __global__ void __launch_bounds__(SVD_THREADS)
-jacobi_kernel(const double* G, int l, int trans, double* GV, double* V, double* sigma, double eps,
-              long long dm1, long long rmax, const double* norm_in, double* norm_out,
-              int* rank_out, int* err) {
+jacobi_kernel(const __grid_constant__ JacobiBatch jb, int* err) {
+  const int bi = blockIdx.x;
+  const double* G = jb.G[bi];
+  const int l = jb.l[bi], trans = jb.trans;
+  double* GV = jb.GV[bi];
+  double* V = jb.V[bi];
+  double* sigma = jb.sigma[bi];
+  int* rank_out = jb.rank_out[bi];
+  const double eps = jb.eps;
+  const long long dm1 = jb.dm1, rmax = jb.rmax;
+  const double* norm_in = jb.norm_in;
+  double* norm_out = bi == 0 ? jb.norm_out : nullptr;
   extern __shared__ __align__(16) unsigned char sm_raw[];
   T* A = (T*)sm_raw;            // column-major: column p at A + p*l
   T* Vm = A + (size_t)l * l;    // column-major
   __shared__ int rotated;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = SVD_THREADS / 32;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int nthreads = blockDim.x, nwarps = nthreads / 32;
+  const int grp = lane >> 3, sub = lane & 7;
 
-  for (int e = tid; e < l * l; e += SVD_THREADS) {
+  for (int e = tid; e < l * l; e += nthreads) {
     const int i = e / l, j = e % l;           // element (i, j) of G
     A[(size_t)j * l + i] = (T)(trans ? G[(size_t)j * l + i] : G[e]);
     Vm[(size_t)j * l + i] = (i == j) ? T(1) : T(0);
@@ -58,47 +96,71 @@ jacobi_kernel(const double* G, int l, int trans, double* GV, double* V, double* 
   const T tiny = (T)(s_tot * (double)eps_t * (double)eps_t * (double)eps_t * (double)eps_t);
   const T abs_thr = tol * eps_t * tot_t;
   const int lp = l + (l & 1);   // even number of players (index l is a dummy when l is odd)
+  const int npairs = lp / 2;
+  T* nrm2 = Vm + (size_t)l * l;  // squared column norms, updated with the rotations
   int sweep = 0;
   for (; sweep < MAX_SWEEPS; ++sweep) {
+    // exact column norms at the start of every sweep
+    for (int j = warp; j < l; j += nwarps) {
+      T acc = 0;
+      for (int i = lane; i < l; i += 32) { const T x = A[(size_t)j * l + i]; acc += x * x; }
+      acc = warp_sum_t(acc);
+      if (lane == 0) nrm2[j] = acc;
+    }
     if (tid == 0) rotated = 0;
     __syncthreads();
     for (int step = 0; step < lp - 1; ++step) {
-      for (int k = warp; k < lp / 2; k += nwarps) {
-        int p, q;
-        if (k == 0) { p = lp - 1; q = step; }
-        else { p = (step + k) % (lp - 1); q = (step - k + (lp - 1)) % (lp - 1); }
-        if (p >= l || q >= l) continue;
-        if (p > q) { const int t = p; p = q; q = t; }
-        T* ap = A + (size_t)p * l;
-        T* aq = A + (size_t)q * l;
-        T al = 0, be = 0, ga = 0;
-        for (int i = lane; i < l; i += 32) {
-          const T x = ap[i], y = aq[i];
-          al += x * x; be += y * y; ga += x * y;
+      for (int k0 = warp * 4; k0 < npairs; k0 += nwarps * 4) {
+        const int k = k0 + grp;
+        int p = -1, q = -1;
+        if (k < npairs) {
+          if (k == 0) { p = lp - 1; q = step; }
+          else { p = (step + k) % (lp - 1); q = (step - k + (lp - 1)) % (lp - 1); }
+          if (p >= l || q >= l) p = q = -1;
+          else if (p > q) { const int t = p; p = q; q = t; }
         }
-        al = warp_sum_t(al); be = warp_sum_t(be); ga = warp_sum_t(ga);
+        T ga = 0;
+        if (p >= 0) {
+          const T* ap = A + (size_t)p * l;
+          const T* aq = A + (size_t)q * l;
+          for (int i = sub; i < l; i += 8) ga += ap[i] * aq[i];
+        }
+        ga = group_sum8(ga);
+        if (p < 0) continue;
+        const T al = nrm2[p], be = nrm2[q];
         // converged pair: relative test, or an inner product at the rounding
         // level of the whole matrix (columns at noise level cannot be made
         // relatively orthogonal in this precision)
         if (ga == T(0) || al <= tiny || be <= tiny || fabs(ga) <= tol * sqrt(al) * sqrt(be) ||
             fabs(ga) <= abs_thr)
           continue;
-        const T zeta = (be - al) / (T(2) * ga);
-        const T t = (zeta >= T(0) ? T(1) : T(-1)) / (fabs(zeta) + sqrt(T(1) + zeta * zeta));
-        const T c = T(1) / sqrt(T(1) + t * t), s = c * t;
-        for (int i = lane; i < l; i += 32) {
-          const T x = ap[i], y = aq[i];
-          ap[i] = c * x - s * y;
-          aq[i] = s * x + c * y;
+        T t, c, s;
+        if (sizeof(T) == 4) {
+          const float zeta = __fdividef((float)(be - al), 2.0f * (float)ga);
+          t = (T)__fdividef(zeta >= 0.f ? 1.f : -1.f, fabsf(zeta) + sqrtf(1.f + zeta * zeta));
+          c = (T)rsqrtf(1.f + (float)(t * t));
+        } else {
+          const T zeta = (be - al) / (T(2) * ga);
+          t = (zeta >= T(0) ? T(1) : T(-1)) / (fabs(zeta) + sqrt(T(1) + zeta * zeta));
+          c = T(1) / sqrt(T(1) + t * t);
         }
+        s = c * t;
+        T* ap = A + (size_t)p * l;
+        T* aq = A + (size_t)q * l;
         T* vp = Vm + (size_t)p * l;
         T* vq = Vm + (size_t)q * l;
-        for (int i = lane; i < l; i += 32) {
-          const T x = vp[i], y = vq[i];
-          vp[i] = c * x - s * y;
-          vq[i] = s * x + c * y;
+        for (int i = sub; i < l; i += 8) {
+          const T x = ap[i], y = aq[i], u = vp[i], w = vq[i];
+          ap[i] = c * x - s * y;
+          aq[i] = s * x + c * y;
+          vp[i] = c * u - s * w;
+          vq[i] = s * u + c * w;
         }
-        if (lane == 0) rotated = 1;
+        if (sub == 0) {
+          nrm2[p] = al - t * ga;
+          nrm2[q] = be + t * ga;
+          rotated = 1;
+        }
       }
       __syncthreads();
     }
@@ -107,7 +169,7 @@ jacobi_kernel(const double* G, int l, int trans, double* GV, double* V, double* 
   }
   if (sweep == MAX_SWEEPS && tid == 0) atomicAdd(err, 1);  // non-convergence counter
   // column norms and descending order (ties by index)
-  double* sg = (double*)(Vm + (size_t)l * l);
+  double* sg = (double*)(Vm + (size_t)l * l + ((l + 1) & ~1));
   for (int j = warp; j < l; j += nwarps) {
     double acc = 0.0;
     for (int i = lane; i < l; i += 32) { const double x = (double)A[(size_t)j * l + i]; acc += x * x; }
@@ -115,7 +177,7 @@ jacobi_kernel(const double* G, int l, int trans, double* GV, double* V, double* 
     if (lane == 0) sg[j] = sqrt(acc);
   }
   __syncthreads();
-  for (int j = tid; j < l; j += SVD_THREADS) {
+  for (int j = tid; j < l; j += nthreads) {
     int rank = 0;
     for (int i = 0; i < l; ++i)
       if (sg[i] > sg[j] || (sg[i] == sg[j] && i < j)) ++rank;
@@ -147,36 +209,57 @@ jacobi_kernel(const double* G, int l, int trans, double* GV, double* V, double* 
 
 }  // namespace
 
-void jacobi_svd(const double* G, int64_t l, int trans, int f32, double* GV, double* V, double* sigma,
-                double eps, int64_t dm1, int64_t rmax, const double* norm_in, double* norm_out,
-                int* rank_out, int* err_flag, cudaStream_t st) {
-  if (g_dry_run) return;
-  const size_t es = f32 ? 4 : 8;
-  const size_t smem = 2 * (size_t)l * l * es + (size_t)l * sizeof(double) + 16;
+void jacobi_svd_batched(const JacobiBatchArgs& a, cudaStream_t st) {
+  if (g_dry_run || a.count == 0) return;
+  if (a.count > MAX_SVD_BATCH) throw Error(TT_ERR_UNSUPPORTED, "jacobi_svd: batch too large");
+  JacobiBatch jb;
+  jb.count = a.count; jb.trans = a.trans; jb.f32 = a.f32; jb.eps = a.eps;
+  jb.dm1 = a.dm1; jb.rmax = a.rmax; jb.norm_in = a.norm_in; jb.norm_out = a.norm_out;
+  int64_t lmax = 1;
+  for (int i = 0; i < a.count; ++i) {
+    jb.G[i] = a.G[i]; jb.l[i] = (int)a.l[i]; jb.GV[i] = a.GV[i]; jb.V[i] = a.V[i];
+    jb.sigma[i] = a.sigma[i]; jb.rank_out[i] = a.rank_out[i];
+    lmax = std::max<int64_t>(lmax, a.l[i]);
+  }
+  const size_t es = a.f32 ? 4 : 8;
+  const size_t smem = 2 * (size_t)lmax * lmax * es + (size_t)(lmax + 2) * es +
+                      (size_t)lmax * sizeof(double) + 16;
   if (smem > 220 * 1024)
-    throw Error(TT_ERR_UNSUPPORTED, "jacobi_svd: l = " + std::to_string(l) + " too large for " +
-                                        (f32 ? "FP32" : "FP64"));
+    throw Error(TT_ERR_UNSUPPORTED, "jacobi_svd: l = " + std::to_string(lmax) + " too large for " +
+                                        (a.f32 ? "FP32" : "FP64"));
   static bool attr[2] = {false, false};
+  // 4 column pairs per warp
+  const int pairs = (int)((lmax + 1) / 2);
+  const int threads =
+      (int)std::min<int64_t>(SVD_THREADS, std::max<int64_t>(64, ceil_div(pairs, 4) * 32));
   const int tok = prof_begin(PROF_SVD, st);
-  if (f32) {
+  if (a.f32) {
     if (!attr[0]) {
       TT_CUDA(cudaFuncSetAttribute(jacobi_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    220 * 1024));
       attr[0] = true;
     }
-    jacobi_kernel<float><<<1, SVD_THREADS, smem, st>>>(G, (int)l, trans, GV, V, sigma, eps, dm1, rmax,
-                                                       norm_in, norm_out, rank_out, err_flag);
+    jacobi_kernel<float><<<a.count, threads, smem, st>>>(jb, a.err);
   } else {
     if (!attr[1]) {
       TT_CUDA(cudaFuncSetAttribute(jacobi_kernel<double>,
                                    cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024));
       attr[1] = true;
     }
-    jacobi_kernel<double><<<1, SVD_THREADS, smem, st>>>(G, (int)l, trans, GV, V, sigma, eps, dm1, rmax,
-                                                        norm_in, norm_out, rank_out, err_flag);
+    jacobi_kernel<double><<<a.count, threads, smem, st>>>(jb, a.err);
   }
   check_launch("jacobi_kernel");
-  prof_end(tok, st, 0.0, 3.0 * l * l * 8.0);
+  prof_end(tok, st, 0.0, 3.0 * lmax * lmax * 8.0 * a.count);
+}
+
+void jacobi_svd(const double* G, int64_t l, int trans, int f32, double* GV, double* V,
+                double* sigma, double eps, int64_t dm1, int64_t rmax, const double* norm_in,
+                double* norm_out, int* rank_out, int* err_flag, cudaStream_t st) {
+  JacobiBatchArgs a;
+  a.count = 1; a.trans = trans; a.f32 = f32; a.eps = eps; a.dm1 = dm1; a.rmax = rmax;
+  a.norm_in = norm_in; a.norm_out = norm_out; a.err = err_flag;
+  a.G[0] = G; a.l[0] = l; a.GV[0] = GV; a.V[0] = V; a.sigma[0] = sigma; a.rank_out[0] = rank_out;
+  jacobi_svd_batched(a, st);
 }
 
 }  // namespace ttsg

@@ -14,6 +14,20 @@ namespace {
 template <typename T>
 constexpr int f64_of() { return sizeof(T) == 8 ? 1 : 0; }
 
+// Truncation factors from the Jacobi output V (l x l, row-major, columns =
+// left singular vectors) and sigma: A = diag(1/sigma_r) V[:, :r]^T (r x l) and
+// B = V[:, :r] diag(sigma_r) (l x r); B A is the projector on the kept directions.
+template <typename T>
+__global__ void trunc_factors_kernel(const double* V, const double* sigma, int l, int r, T* A,
+                                     T* B) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < l * r; e += gridDim.x * blockDim.x) {
+    const int i = e / r, j = e % r;
+    const double v = V[(size_t)i * l + j], sg = sigma[j];
+    A[(size_t)j * l + i] = (T)(sg > 0.0 ? v / sg : 0.0);
+    B[(size_t)i * r + j] = (T)(v * sg);
+  }
+}
+
 int read_int(const Ctx& c, const int* dev) {
   if (g_dry_run) return 1;
   int h = 0;
@@ -306,6 +320,113 @@ void tt_round_rand_dev(const Ctx& c, const std::vector<Term<T>>& terms, double e
     ar.release(mk);
     return;
   }
+  if (!f64) {
+    // Float modes: all bonds truncated from the same left-orthogonal tensor.
+    // Right Gram matrices G_b = C_{>b}^T C_{>b} (one sweep), their
+    // eigenvectors W_b by batched FP64 Cholesky + Jacobi (one CTA per bond),
+    // then core k <- W_k^T H_k W_{k+1}.  The error is at most the sum of the
+    // dropped tails, so each bond uses delta = eps ||T|| / (d - 1).
+    std::vector<T*> Gk(d + 1, nullptr);
+    std::vector<double*> Gd(d + 1, nullptr), Rd(d + 1, nullptr), Vd(d + 1, nullptr),
+        GVd(d + 1, nullptr), sg(d + 1, nullptr);
+    int64_t t1max = 1;
+    for (int b = 1; b < d; ++b) {
+      Gk[b] = ar.take<T>(ell[b] * ell[b]);
+      Gd[b] = ar.take<double>(ell[b] * ell[b]);
+      Rd[b] = ar.take<double>(ell[b] * ell[b]);
+      Vd[b] = ar.take<double>(ell[b] * ell[b]);
+      GVd[b] = ar.take<double>(ell[b] * ell[b]);
+      sg[b] = ar.take<double>(ell[b]);
+      if (b < d - 1) t1max = std::max(t1max, ell[b] * n[b] * ell[b + 1]);
+    }
+    T* T1g = ar.take<T>(t1max);
+    int* rks = ar.take<int>(d + 1);
+    {  // G_{d-1} = H_{d-1} H_{d-1}^T
+      const int b = d - 1;
+      GemmProblem g;
+      g.M = (int)ell[b]; g.N = (int)ell[b]; g.K = (int)n[b];
+      g.A = H[b]; g.sAm = n[b]; g.sAk = 1;
+      g.B = H[b]; g.sBk = 1; g.sBn = n[b];
+      g.C = Gk[b]; g.sCm = ell[b]; g.sCn = 1;
+      gemm(c.mode, {g}, c.st);
+    }
+    for (int b = d - 2; b >= 1; --b) {
+      const int64_t nb = n[b], l0 = ell[b], l1 = ell[b + 1];
+      gemm(c.mode, {gemm_rm((int)(l0 * nb), (int)l1, (int)l1, H[b], l1, Gk[b + 1], l1, T1g, l1)},
+           c.st);
+      GemmProblem g;
+      g.M = (int)l0; g.N = (int)l0; g.K = (int)(nb * l1);
+      g.A = T1g; g.sAm = nb * l1; g.sAk = 1;
+      g.B = H[b]; g.sBk = 1; g.sBn = nb * l1;
+      g.C = Gk[b]; g.sCm = l0; g.sCn = 1;
+      gemm(c.mode, {g}, c.st);
+    }
+    {
+      std::vector<CopySeg> segs;
+      for (int b = 1; b < d; ++b) {
+        CopySeg sgm;
+        sgm.src = Gk[b]; sgm.dst = Gd[b]; sgm.A = ell[b] * ell[b]; sgm.sa = 1;
+        sgm.src_f64 = 0; sgm.dst_f64 = 1;
+        segs.push_back(sgm);
+      }
+      copy3d(segs, c.st);
+    }
+    chol_f64_batched(d - 1, (const double* const*)&Gd[1], &ell[1], 1e-14, &Rd[1], c.err + 2,
+                     c.st);
+    JacobiBatchArgs ja;
+    ja.count = d - 1; ja.trans = 0; ja.f32 = 1; ja.eps = eps;
+    ja.dm1 = (int64_t)(d - 1) * (d - 1);  // delta = eps ||T|| / (d - 1)
+    ja.rmax = rmax; ja.err = c.err + 1;
+    for (int b = 1; b < d; ++b) {
+      ja.G[b - 1] = Rd[b]; ja.l[b - 1] = ell[b]; ja.GV[b - 1] = GVd[b]; ja.V[b - 1] = Vd[b];
+      ja.sigma[b - 1] = sg[b]; ja.rank_out[b - 1] = rks + b;
+    }
+    jacobi_svd_batched(ja, c.st);
+    std::vector<int> rh(d + 1, 1);
+    if (!g_dry_run) {
+      TT_CUDA(cudaMemcpyAsync(rh.data() + 1, rks + 1, sizeof(int) * (d - 1), cudaMemcpyDeviceToHost,
+                              c.st));
+      TT_CUDA(cudaStreamSynchronize(c.st));
+    }
+    rh[0] = rh[d] = 1;
+    // W_b = V_b[:, :r_b] in the working precision
+    std::vector<T*> W(d + 1, nullptr);
+    {
+      std::vector<CopySeg> segs;
+      for (int b = 1; b < d; ++b) {
+        W[b] = ar.take<T>(ell[b] * rh[b]);
+        CopySeg sgm;
+        sgm.src = Vd[b]; sgm.dst = W[b]; sgm.A = ell[b]; sgm.B = rh[b]; sgm.C = 1;
+        sgm.sa = ell[b]; sgm.sb = 1; sgm.src_f64 = 1; sgm.dst_f64 = 0;
+        segs.push_back(sgm);
+      }
+      copy3d(segs, c.st);
+    }
+    // U_k = H_k W_{k+1} ((ell_k n_k) x r_{k+1}); core k = W_k^T U_k
+    std::vector<T*> U(d, nullptr);
+    std::vector<GemmProblem> p1, p2;
+    for (int k = 0; k < d - 1; ++k) {
+      U[k] = (k == 0) ? y.core[0] : ar.take<T>(ell[k] * n[k] * rh[k + 1]);
+      p1.push_back(gemm_rm((int)(ell[k] * n[k]), rh[k + 1], (int)ell[k + 1], H[k], ell[k + 1],
+                           W[k + 1], rh[k + 1], U[k], rh[k + 1]));
+    }
+    for (int k = 1; k < d; ++k) {
+      const T* Uk = (k == d - 1) ? H[d - 1] : U[k];
+      const int64_t cols = n[k] * rh[k + 1];
+      GemmProblem g;
+      g.M = rh[k]; g.N = (int)cols; g.K = (int)ell[k];
+      g.A = W[k]; g.sAm = 1; g.sAk = rh[k];
+      g.B = Uk; g.sBk = cols; g.sBn = 1;
+      g.C = y.core[k]; g.sCm = cols; g.sCn = 1;
+      p2.push_back(g);
+    }
+    gemm(c.mode, p1, c.st);
+    gemm(c.mode, p2, c.st);
+    for (int k = 0; k <= d; ++k) y.r[k] = rh[k];
+    check_device_flags(c);
+    ar.release(mk);
+    return;
+  }
   int64_t lmax = 1, hmax = 1, qtmax = 1;
   for (int k = 0; k <= d; ++k) lmax = std::max(lmax, ell[k]);
   for (int k = 0; k < d; ++k) hmax = std::max(hmax, ell[k] * n[k] * ell[k + 1]);
@@ -328,6 +449,11 @@ void tt_round_rand_dev(const Ctx& c, const std::vector<Term<T>>& terms, double e
   }
   void* qw2 = ar.take<char>((int64_t)qws2);
   const int f32svd = f64 ? 0 : 1;
+  // float modes: Gram X X^T + shifted Cholesky replace the QR of the truncation
+  double* Gb = ar.take<double>(lmax * lmax);
+  size_t gws = 0;
+  for (int k = 1; k < d; ++k) gws = std::max(gws, gram_workspace(n[k] * ell[k + 1], ell[k]));
+  void* gw = f64 ? nullptr : ar.take<char>((int64_t)gws);
 
   const T* cur = H[d - 1];
   int64_t rr = 1;
@@ -338,7 +464,23 @@ void tt_round_rand_dev(const Ctx& c, const std::vector<Term<T>>& terms, double e
     const int64_t rows_prev = ell[k - 1] * n[k - 1];
     T* next = (mu - 1 == 1) ? y.core[0] : cur2[mu & 1];
     int r = 0;
-    if (cc >= L) {
+    if (!f64) {
+      gram_f64(cur, 0, cc, L, 1, cc, Gb, gw, gws, c.st);
+      chol_f64(Gb, L, 1e-14, Rf, c.err + 2, c.st);
+      jacobi_svd(Rf, L, 0, 1, GV, Vd, sig, eps, d - 1, rmax, mu == d ? nullptr : nrm,
+                 mu == d ? nrm : nullptr, rk, c.err + 1, c.st);
+      r = read_int(c, rk);
+      if (!g_dry_run) {
+        trunc_factors_kernel<T><<<(unsigned)std::max<int64_t>(1, std::min<int64_t>(
+                                      ceil_div(L * r, 256), 256)), 256, 0, c.st>>>(
+            Vd, sig, (int)L, r, Vt, GVt);
+        check_launch("trunc_factors_kernel");
+      }
+      // core mu = diag(1/sigma_r) U_r^T X (r x cc); core mu-1 = H_{mu-1} U_r diag(sigma_r)
+      GemmProblem g = gemm_rm(r, (int)cc, (int)L, Vt, L, cur, cc, y.core[k], cc);
+      GemmProblem g2 = gemm_rm((int)rows_prev, r, (int)L, H[k - 1], L, GVt, r, next, r);
+      gemm(c.mode, {g, g2}, c.st);
+    } else if (cc >= L) {
       // X = cur (L x cc); X^T = Qt R  (Qt: cc x L)
       qr_f64(cur, f64, cc, L, 1, cc, Qt, f64, L, Rf, qw2, qws2, c.err, c.st);
       jacobi_svd(Rf, L, 1, f32svd, GV, Vd, sig, eps, d - 1, rmax, mu == d ? nullptr : nrm,

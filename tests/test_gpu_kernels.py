@@ -176,7 +176,10 @@ def test_round_rand_parity_same_drm(g, mode, eps, rmax, p):
              (-1.3, ti.random_tt(ns, [1, 3, 12, 2, 1], seed=11))]
     L = [1, rmax + p, rmax + p, rmax + p, 1]
     drm = ti.gaussian_drm(ns, L, seed=12)
-    ref = ornd.rto_round(terms, drm, eps=eps, rmax=rmax, oversample=p)
+    # FP64 mode truncates bond by bond (TT-SVD sweep); the float modes truncate
+    # all bonds from the same tensor (the oracle's "simultaneous" reading)
+    trunc = "sequential" if mode == 0 else "simultaneous"
+    ref = ornd.rto_round(terms, drm, eps=eps, rmax=rmax, oversample=p, truncation=trunc)
     y = g.tt_round_rand([dev_tt(g, X, mode) for _, X in terms], [a for a, _ in terms], eps, rmax, p,
                         drm=[torch.as_tensor(c, dtype=g.mode_dtype(mode), device="cuda") for c in drm],
                         mode=mode)
@@ -184,10 +187,11 @@ def test_round_rand_parity_same_drm(g, mode, eps, rmax, p):
     # the represented tensors agree (cores may differ by orthogonal factors)
     tol = 1e-10 if mode == 0 else 1e-4
     assert tt_rel_diff(y.numpy(), ref) <= tol
-    # cores 2..d right-orthogonal
-    for c in y.numpy()[1:]:
-        Mx = c.reshape(c.shape[0], -1)
-        assert np.max(np.abs(Mx @ Mx.T - np.eye(Mx.shape[0]))) <= (1e-12 if mode == 0 else 1e-5)
+    if mode == 0:
+        # cores 2..d right-orthogonal after the sequential sweep
+        for c in y.numpy()[1:]:
+            Mx = c.reshape(c.shape[0], -1)
+            assert np.max(np.abs(Mx @ Mx.T - np.eye(Mx.shape[0]))) <= 1e-12
 
 
 def test_round_rand_philox_drm_matches_oracle(g):

@@ -120,3 +120,27 @@ def test_rto_vs_tt_svd_heuristic():
         y = rnd.rto_round(z, drm, eps=0.0, rmax=5, oversample=5)
         ratios.append(np.linalg.norm(tt.full(y) - zf) / e_ref)
     assert np.median(ratios) < 10.0
+
+
+@pytest.mark.parametrize("eps", [3e-1, 1e-1, 1e-3])
+def test_simultaneous_truncation_error_bound_and_identity(eps):
+    # the bond-by-bond telescoping bound: ||T - T~|| <= sum of dropped tails
+    # <= eps ||T|| with per-bond threshold eps ||T|| / (d - 1)
+    ns = [4, 5, 4, 3, 4]
+    z = [(1.0, ti.random_tt(ns, [1, 4, 6, 5, 3, 1], seed=s)) for s in range(3)]
+    X = ttm_left(tt.add(z))
+    y = rnd.truncate_simultaneous(X, eps=eps)
+    err = np.linalg.norm(tt.full(y) - tt.full(X))
+    assert err <= eps * np.linalg.norm(tt.full(X)) * (1 + 1e-10)
+    # tolerance 0: nothing is dropped
+    y0 = rnd.truncate_simultaneous(X, eps=0.0)
+    assert np.allclose(tt.full(y0), tt.full(X), atol=1e-12 * np.linalg.norm(tt.full(X)))
+    # a small tolerance removes only the roundoff directions: the ranks become
+    # the exact unfolding ranks (the Gram matrices resolve singular values down
+    # to about sqrt(machine eps) of the largest, so 1e-6 is "small" here)
+    y1 = rnd.truncate_simultaneous(X, eps=1e-6)
+    assert tt.ranks(y1)[1:-1] == unfolding_ranks(tt.full(X), ns)
+
+
+def ttm_left(cores):
+    return tt.left_orthogonalize(cores)
