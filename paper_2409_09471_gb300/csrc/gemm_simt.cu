@@ -242,6 +242,11 @@ void set_gemm_scratch(void* ws, size_t bytes) {
   g_split_bytes = ws ? bytes : 0;
 }
 
+void gemm_fp32_simt(const std::vector<GemmProblem>& probs, cudaStream_t st) {
+  if (g_dry_run) return;
+  launch_simt<float>(probs, st);
+}
+
 void gemm(int mode, const std::vector<GemmProblem>& probs, cudaStream_t st) {
   if (g_dry_run) return;
   if (mode == TT_MODE_FP64) launch_simt<double>(probs, st);

@@ -1,13 +1,329 @@
-// Tensor-core (tcgen05, TF32 with FP32 accumulation) path of the grouped GEMM.
+// Tensor-core contractions for TT_MODE_TF32: the TT matvec core contraction
+// (Section 2.2, matvec formula) on tcgen05 in TF32 with FP32 accumulation.
+//
+// Per core k the contraction is a batch over (a, l) of GEMMs
+//   G[(a,l)][(i,a')][l'] = sum_j Dp[a][(i,a')][j] * Ct[l][l'][j],
+// with both operands K-major (j innermost): the working operator layout
+// [a][i][a'][j] already is, and the vector core C[l][j][l'] is first copied to
+// Ct[l][l'][j].  One CTA computes a 128 x 64 output tile: thread 0 issues the
+// TMA loads (128-byte swizzle, 32 FP32 values of K per row) and the tcgen05.mma
+// instructions (M=128, N=64, K=8 each) into a TMEM accumulator, and the four
+// warps read the accumulator back with tcgen05.ld for the epilogue.  Rows and
+// columns outside the tile's batch entry are computed on zero-filled or
+// neighbouring data and never stored.
+//
+// Split TF32 (the three-product error compensation of Ootomo and Yokota,
+// "Recovering single precision accuracy from Tensor Cores while surpassing the
+// FP32 theoretical peak performance", 2022): after each tile lands, the CTA
+// splits every FP32 value x in shared memory into hi = x with the low 13
+// mantissa bits cleared (exactly a TF32 value) and lo = x - hi (exact in FP32),
+// and accumulates hi*hi + lo*hi + hi*lo.  The dropped lo*lo term and the TF32
+// rounding of lo are below 2^-20 relative, against 2^-11 for plain TF32: the
+// matvec defines the operator of the Krylov solve, and its relative error times
+// the condition number is the contraction factor of each refinement cycle.
+//
+// Every mbarrier wait is bounded; on expiry the CTA sets bit 2 of the error
+// word, waits (bounded) for its own copies, frees its TMEM and returns.
 #include "common.cuh"
+#include "prof.cuh"
+#include <cuda.h>
+#include <cudaTypedefs.h>
 
 namespace ttsg {
 
-void gemm_tf32(const std::vector<GemmProblem>& probs, cudaStream_t st) {
-  (void)probs;
-  (void)st;
+namespace {
+
+constexpr int TM = 128, TN = 64, TK = 32;       // tile: rows, columns, K per TMA box
+constexpr int TC_THREADS = 128;
+constexpr long long WAIT_LIMIT = 1ll << 22;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+// Bounded wait for the given phase parity; returns false on expiry.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  const uint32_t a = smem_u32(bar);
+  for (long long it = 0; it < WAIT_LIMIT; ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar,
+                                            int x, int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_u32(dst)),
+      "l"((uint64_t)map), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// Shared-memory matrix descriptor, K-major, 128-byte swizzle: start address,
+// leading byte offset 16 (unused inside one swizzle row), stride byte offset
+// 1024 (8 rows of 128 bytes), descriptor version 1, layout type 2 (SW128).
+__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t addr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((addr & 0x3FFFF) >> 4);
+  d |= (uint64_t)(16 >> 4) << 16;
+  d |= (uint64_t)(1024 >> 4) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)2 << 61;
+  return d;
+}
+
+// Instruction descriptor for kind::tf32: D F32, A and B TF32, both K-major.
+__host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
+  return (1u << 4)             // D format F32
+         | (2u << 7)           // A format TF32
+         | (2u << 10)          // B format TF32
+         | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+struct MatvecTC {
+  int M;        // n * R1 rows of one operator slice (i, a')
+  int N;        // r1
+  int K;        // n
+  int r0, R0;   // batch: a in [0, R0), l in [0, r0)
+  float* G;     // output core
+  int* err;
+};
+
+// hi/lo split of one staged tile, elementwise (so the swizzled layout is
+// kept): hi keeps sign, exponent and the 10 leading mantissa bits.
+__device__ __forceinline__ void split_tf32(float* hi, float* lo, int count) {
+  for (int e = threadIdx.x * 4; e < count; e += TC_THREADS * 4) {
+    float4 v = *reinterpret_cast<float4*>(hi + e);
+    float4 h, r;
+    h.x = __uint_as_float(__float_as_uint(v.x) & 0xFFFFE000u);
+    h.y = __uint_as_float(__float_as_uint(v.y) & 0xFFFFE000u);
+    h.z = __uint_as_float(__float_as_uint(v.z) & 0xFFFFE000u);
+    h.w = __uint_as_float(__float_as_uint(v.w) & 0xFFFFE000u);
+    r.x = v.x - h.x; r.y = v.y - h.y; r.z = v.z - h.z; r.w = v.w - h.w;
+    *reinterpret_cast<float4*>(hi + e) = h;
+    *reinterpret_cast<float4*>(lo + e) = r;
+  }
+}
+
+__global__ void __launch_bounds__(TC_THREADS, 1)
+matvec_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
+                 const MatvecTC p) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  // 1024-byte aligned tiles for the 128-byte swizzle: [A hi | B hi | A lo | B lo]
+  unsigned char* base =
+      (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  constexpr int TILE = (TM + TN) * TK;        // floats of one A+B stage (24 KB)
+  float* sA = (float*)base;                    // [TM][TK] swizzled, 16 KB
+  float* sB = sA + TM * TK;                    // [TN][TK] swizzled, 8 KB
+  float* sAl = sA + TILE;
+  float* sBl = sAl + TM * TK;
+  __shared__ __align__(8) uint64_t bar_full, bar_mma;
+  __shared__ uint32_t tmem_base;
+  __shared__ int fail;
+
+  const int tiles_m = (p.M + TM - 1) / TM, tiles_n = (p.N + TN - 1) / TN;
+  const int tm = blockIdx.x % tiles_m, tn = blockIdx.x / tiles_m;
+  if (tn >= tiles_n) return;
+  const int a = blockIdx.y / p.r0, l = blockIdx.y % p.r0;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(&tmem_base)),
+                 "r"(TN));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (threadIdx.x == 0) {
+    fail = 0;
+    mbar_init(&bar_full, 1);
+    mbar_init(&bar_mma, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_base;
+
+  const int ktiles = (p.K + TK - 1) / TK;
+  const int rowA = a * p.M + tm * TM;      // operator rows of slice a
+  const int rowB = l * p.N + tn * TN;      // rows (l, l') of Ct
+  uint32_t phase = 0;
+  int stage = 0;                           // 1: copies issued, 2: MMAs issued
+  for (int kt = 0; kt < ktiles; ++kt) {
+    if (threadIdx.x == 0) {
+      mbar_expect_tx(&bar_full, TILE * 4);
+      tma_load_2d(sA, &mapA, &bar_full, kt * TK, rowA);
+      tma_load_2d(sB, &mapB, &bar_full, kt * TK, rowB);
+    }
+    stage = 1;
+    const bool landed = mbar_wait(&bar_full, phase);
+    if (__syncthreads_or(!landed)) break;
+    split_tf32(sA, sAl, TILE);
+    // generic-proxy writes of the split tiles become visible to the MMA unit
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t idesc = idesc_tf32(TM, TN);
+      const uint64_t dA[2] = {smem_desc_sw128(smem_u32(sA)), smem_desc_sw128(smem_u32(sAl))};
+      const uint64_t dB[2] = {smem_desc_sw128(smem_u32(sB)), smem_desc_sw128(smem_u32(sBl))};
+#pragma unroll
+      for (int kk = 0; kk < TK / 8; ++kk) {
+        // advance 8 TF32 values (32 bytes) along K inside the swizzle row
+        const uint64_t off = (uint64_t)((kk * 32) >> 4);
+#pragma unroll
+        for (int t = 0; t < 3; ++t) {
+          // t = 0: hi*hi, 1: lo*hi, 2: hi*lo
+          const uint64_t da = dA[t == 1 ? 1 : 0] + off;
+          const uint64_t db = dB[t == 2 ? 1 : 0] + off;
+          const uint32_t acc = (kt > 0 || kk > 0 || t > 0) ? 1u : 0u;
+          asm volatile(
+              "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
+              " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+              "l"(da), "l"(db), "r"(idesc), "r"(acc)
+              : "memory");
+        }
+      }
+      asm volatile(
+          "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+              smem_u32(&bar_mma))
+          : "memory");
+    }
+    stage = 2;
+    // every thread waits: the next copy and split overwrite the tiles the MMAs read
+    const bool done = mbar_wait(&bar_mma, phase);
+    if (__syncthreads_or(!done)) break;
+    stage = 0;
+    phase ^= 1u;
+  }
+  if (stage != 0 && threadIdx.x == 0) {
+    fail = 1;
+    atomicOr(p.err, 4);
+    // let copies or MMAs still in flight land before the CTA leaves
+    mbar_wait(&bar_full, phase);
+    if (stage == 2) mbar_wait(&bar_mma, phase);
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+
+  if (!fail) {
+    // epilogue: warp w owns accumulator lanes (rows) 32w .. 32w+31
+    const int m = tm * TM + warp * 32 + lane;
+    const int64_t out_base = ((int64_t)(a * p.r0 + l) * p.M + m) * p.N;
+#pragma unroll
+    for (int c0 = 0; c0 < TN; c0 += 16) {
+      uint32_t r[16];
+      const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x16.b32"
+          " {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+          : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+            "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+            "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+          : "r"(taddr));
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      if (m < p.M) {
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+          const int n = tn * TN + c0 + q;
+          if (n < p.N) p.G[out_base + n] = __uint_as_float(r[q]);
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TN));
+  }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    cudaDriverEntryPointQueryResult q;
+    void* p = nullptr;
+    TT_CUDA(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000,
+                                             cudaEnableDefault, &q));
+    if (q != cudaDriverEntryPointSuccess || !p)
+      throw Error(TT_ERR_CUDA, "cuTensorMapEncodeTiled is not available");
+    fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+  }
+  return fn;
+}
+
+// 2-D FP32 tensor map: inner dimension K (contiguous), outer `rows` with row
+// stride `ld` floats; box TK x box_rows, 128-byte swizzle, zero fill outside.
+CUtensorMap make_map(const float* ptr, int64_t K, int64_t rows, int64_t ld, int box_rows) {
+  if (((uintptr_t)ptr & 15) || ((ld * 4) & 15))
+    throw Error(TT_ERR_UNSUPPORTED, "tensor map: base or row stride not 16-byte aligned");
+  CUtensorMap m;
+  cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)(ld * 4)};
+  cuuint32_t box[2] = {(cuuint32_t)TK, (cuuint32_t)box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = encode_fn()(&m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void*)ptr, dims, strides, box,
+                           estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) throw Error(TT_ERR_CUDA, "cuTensorMapEncodeTiled failed");
+  return m;
+}
+
+}  // namespace
+
+bool matvec_tc_supported(int64_t n, int64_t r1) {
+  // K-major rows must be 16-byte multiples (n % 4 == 0) for the tensor maps
+  return (n % 4) == 0 && n >= 8 && r1 >= 1;
+}
+
+// One core: G (R0 r0 x n x R1 r1) from Dp ([R0][n R1][n]) and Ct ([r0][r1][n]).
+void matvec_core_tc(const float* Dp, const float* Ct, float* G, int64_t n, int64_t R0, int64_t R1,
+                    int64_t r0, int64_t r1, int* err, cudaStream_t st) {
   if (g_dry_run) return;
-  throw Error(TT_ERR_UNSUPPORTED, "TF32 tensor-core GEMM not built yet");
+  const int64_t M = n * R1;
+  CUtensorMap mA = make_map(Dp, n, R0 * M, n, TM);
+  CUtensorMap mB = make_map(Ct, n, r0 * r1, n, TN);
+  MatvecTC p;
+  p.M = (int)M; p.N = (int)r1; p.K = (int)n; p.r0 = (int)r0; p.R0 = (int)R0; p.G = G; p.err = err;
+  const int tiles = (int)(ceil_div(M, TM) * ceil_div(r1, TN));
+  const size_t smem = (size_t)2 * (TM + TN) * TK * 4 + 1024;
+  static bool attr = false;
+  if (!attr) {
+    TT_CUDA(cudaFuncSetAttribute(matvec_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem));
+    attr = true;
+  }
+  const int tok = prof_begin(PROF_GEMM, st);
+  matvec_tc_kernel<<<dim3(tiles, (unsigned)(R0 * r0)), TC_THREADS, smem, st>>>(mA, mB, p);
+  check_launch("matvec_tc_kernel");
+  prof_end(tok, st, 2.0 * M * r1 * n * R0 * r0,  // algorithmic flops (one product)
+           4.0 * (R0 * M * n + r0 * r1 * n + R0 * r0 * M * r1));
+}
+
+// Grouped GEMMs other than the matvec run on the FP32 CUDA-core kernel in
+// TF32 mode (their operands are strided views the tensor maps do not cover).
+void gemm_fp32_simt(const std::vector<GemmProblem>& probs, cudaStream_t st);
+void gemm_tf32(const std::vector<GemmProblem>& probs, cudaStream_t st) {
+  gemm_fp32_simt(probs, st);
 }
 
 }  // namespace ttsg

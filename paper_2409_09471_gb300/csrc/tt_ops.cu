@@ -49,6 +49,34 @@ void check_device_flags(const Ctx& c) {
 template <typename T>
 void tt_matvec_dev(const Ctx& c, const TTop<T>& A, const TTv<T>& x, const TTv<T>& y) {
   std::vector<GemmProblem> ps;
+  if (c.mode == TT_MODE_TF32 && sizeof(T) == 4) {
+    // tensor cores: per core, Ct[l][l'][j] = C[l][j][l'] then the tcgen05 GEMM
+    const size_t mk = c.ar->mark();
+    for (int k = 0; k < x.d; ++k) {
+      const int64_t n = x.n[k], R0 = A.R[k], R1 = A.R[k + 1], r0 = x.r[k], r1 = x.r[k + 1];
+      if (!matvec_tc_supported(n, r1)) continue;
+      float* Ct = c.ar->take<float>(r0 * r1 * n);
+      CopySeg sg;
+      sg.src = x.core[k]; sg.dst = Ct; sg.A = r0; sg.B = r1; sg.C = n;
+      sg.sa = n * r1; sg.sb = 1; sg.sc = r1;
+      copy3d({sg}, c.st);
+      matvec_core_tc((const float*)A.core[k], Ct, (float*)y.core[k], n, R0, R1, r0, r1, c.err,
+                     c.st);
+    }
+    c.ar->release(mk);
+    for (int k = 0; k < x.d; ++k) {
+      if (matvec_tc_supported(x.n[k], x.r[k + 1])) continue;
+      const int64_t n = x.n[k], R0 = A.R[k], R1 = A.R[k + 1], r0 = x.r[k], r1 = x.r[k + 1];
+      GemmProblem g;
+      g.M = (int)(n * R1); g.N = (int)r1; g.K = (int)n; g.nb1 = (int)R0; g.nb2 = (int)r0;
+      g.A = A.core[k]; g.sAm = n; g.sAk = 1; g.sAb1 = n * R1 * n; g.sAb2 = 0;
+      g.B = x.core[k]; g.sBk = r1; g.sBn = 1; g.sBb1 = 0; g.sBb2 = n * r1;
+      g.C = y.core[k]; g.sCm = r1; g.sCn = 1; g.sCb1 = r0 * n * R1 * r1; g.sCb2 = n * R1 * r1;
+      ps.push_back(g);
+    }
+    gemm(c.mode, ps, c.st);
+    return;
+  }
   for (int k = 0; k < x.d; ++k) {
     const int64_t n = x.n[k], R0 = A.R[k], R1 = A.R[k + 1], r0 = x.r[k], r1 = x.r[k + 1];
     GemmProblem g;

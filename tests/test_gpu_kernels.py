@@ -3,7 +3,10 @@ the C ABI: Philox Gaussian stream, TT matvec, Khatri-Rao sketch, TT inner
 product, FP64 Householder QR, sketched least squares and randomized rounding.
 
 Tolerances: FP64 mode 1e-12 relative per kernel; FP32 mode 2e-5 relative
-(float32 accumulation over at most a few thousand terms)."""
+(float32 accumulation over at most a few thousand terms); TF32 mode 3e-5: the
+tensor-core matvec splits each operand into two TF32 parts and keeps three
+products, so each product carries at most about 2^-20 relative error (plain
+TF32 would be 2^-11 = 4.9e-4) before the same float32 accumulation."""
 import numpy as np
 import pytest
 import torch
@@ -15,6 +18,7 @@ pytestmark = pytest.mark.gpu
 
 F64_TOL = 1e-12
 F32_TOL = 2e-5
+TF32_TOL = 3e-5   # split TF32 (hi*hi + lo*hi + hi*lo) with FP32 accumulation
 
 
 @pytest.fixture(scope="module")
@@ -34,7 +38,7 @@ def rel_err(a, b):
 
 
 def tol_of(g, mode):
-    return F64_TOL if mode == g.MODE_FP64 else F32_TOL
+    return {0: F64_TOL, 1: F32_TOL, 2: TF32_TOL}[mode]
 
 
 def tt_rel_diff(a_cores, b_cores):
@@ -70,7 +74,23 @@ def test_matvec_parity(g, mode, d, n, ranks):
         assert rel_err(a, b) <= tol_of(g, mode)
 
 
-@pytest.mark.parametrize("mode", [0, 1])
+@pytest.mark.parametrize("d,n,ranks", [(3, 64, [1, 64, 37, 1]), (3, 16, [1, 5, 100, 1]),
+                                       (4, 32, [1, 1, 3, 130, 1]), (2, 128, [1, 9, 1])])
+def test_matvec_parity_tensor_cores(g, d, n, ranks):
+    # n a multiple of 4 takes the tcgen05 path in TF32 mode (two N tiles when
+    # the rank exceeds 64, two M tiles when n R > 128)
+    M = ti.laplacian_1d(n) + 10 * ti.central_difference_1d(n)
+    op = ti.kron_sum_operator([M] * d)
+    op[1] = np.random.default_rng(3).standard_normal(op[1].shape)
+    x = ti.random_tt([n] * d, ranks, seed=4)
+    ref = ott.matvec(op, x)
+    y = g.tt_matvec(g.op_to_device(op, torch.float32), dev_tt(g, x, 2), mode=2)
+    assert y.ranks == ott.ranks(ref)
+    for a, b in zip(y.numpy(), ref):
+        assert rel_err(a, b) <= TF32_TOL
+
+
+@pytest.mark.parametrize("mode", [0, 1, 2])
 def test_matvec_full_size_eigenvector(g, mode):
     # d=10, n=64 (the convection-diffusion workload's operator): A q = lambda q
     # exactly for a rank-1 tensor of eigenvectors; sampled entries are checked.

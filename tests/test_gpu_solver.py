@@ -66,3 +66,13 @@ def test_convdiff_full_size_fp32(g):
     assert res <= 1e-6
     assert abs(res - info["true_res"]) <= 1e-2 * res
     assert info["max_rank"] <= w.params["rmax"]
+
+
+def test_convdiff_full_size_tf32(g):
+    # mixed precision: tcgen05 TF32 matvec, FP32 elsewhere, FP64 QR / least
+    # squares / residual, refinement restarts until the true residual is met
+    w = ti.workload("convdiff")
+    x, info = solve(g, w, g.MODE_TF32)
+    assert info["status"] == 0
+    res = osol.true_residual_norm(w.op, x.numpy(), w.b) / ott.norm(w.b)
+    assert res <= 1e-6
