@@ -220,7 +220,7 @@ def run_ours(args):
         s_it, its, cores, dt = oracle_sample(args.cpu_seconds, "baseline")
         cpu = (s_it, its, cores, dt)
 
-    mode_name = args.mode or os.environ.get("TTSG_MODE", "fp32")
+    mode_name = args.mode or os.environ.get("TTSG_MODE", "tf32")
     mode = {"tf32": g.MODE_TF32, "fp32": g.MODE_FP32, "fp64": g.MODE_FP64}[mode_name]
     w, p = workload()
     op = g.op_to_device(w.op)

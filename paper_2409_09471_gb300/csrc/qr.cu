@@ -3,26 +3,32 @@
 // The rounding of Section 3.3 orthogonalises the sketch Y = Z W (l columns, up
 // to l_{mu-1} n_mu rows) once per bond, and the truncation sweep factorises the
 // transposed core unfoldings the same way.  On GB300 the FP64 pipe delivers
-// about 8 GFLOP/s per SM, so the factorisation is spread over up to one CTA
-// per SM: CTA c keeps a contiguous block of rows in shared memory (FP64).
+// about 2 FMA per clock per SM, so the factorisation is spread over up to one
+// CTA per SM: CTA c keeps a contiguous block of rows in shared memory (FP64),
+// and every FP64 instruction that is not an FMA of the factorisation itself
+// counts.
 //
 // Reflector convention (LAPACK dlarfg): for x = Y[j:, j] with alpha = x_0,
 // sigma^2 = ||x_{1:}||^2: beta = -sign(alpha) sqrt(alpha^2 + sigma^2),
-// tau = (beta - alpha) / beta, v = [1; x_{1:} / (alpha - beta)];
-// sigma^2 == 0 gives tau = 0 (identity).  R's diagonal holds beta.
+// tau = (beta - alpha) / beta, v = [1; x_{1:} / (alpha - beta)]; sigma^2 == 0
+// gives tau = 0 (identity).  R's diagonal holds beta.
 //
-// Synchronisation.  Cross-CTA sums go through FP64 atomics into per-column
-// slots that are zeroed before the launch, so every CTA reads one finished
-// value after a grid barrier (all CTAs read the same memory, hence build the
-// same reflector).  Factorisation step j needs one barrier: besides the
-// products w = v^T Y[:, j+1:], each CTA contributes the three sums that give
-// the next column's norm after the update, sigma^2_{j+1} = S1 - 2 tau w S2 +
-// tau^2 w^2 S3 (S1 = sum Y^2, S2 = sum v Y, S3 = sum v^2 over rows > j+1).  When
-// that downdate could lose accuracy (sigma^2 < S1 / 100) the norm is recomputed
-// exactly with a second barrier; the decision is uniform across CTAs.
-// The explicit Q = H_0 ... H_{l-1} [I; 0] is accumulated backwards in blocks
-// of QB reflectors in the compact-WY form I - V T V^T (T from the block's
-// V^T V), one barrier per block.
+// One grid-wide reduction per column.  At step j every CTA sums, over its rows
+// r > j, t_c = Y[r][j] Y[r][c] for all columns c (FP64 atomics into replicated
+// per-step slots), and the owner of row j publishes that row.  With scale =
+// 1 / (alpha - beta) the same formula u_c = Y[j][c] + scale t_c gives
+//   c > j:  v^T Y[:, c], the product the reflector update needs, and
+//   c < j:  V[:, c]^T v, the column of the compact-WY factor T
+//           (H_0 ... H_j = I - V T V^T, T[0:j, j] = -tau_j T[0:j, 0:j] V^T v_j),
+// because column c < j already holds the normalised reflector below its
+// diagonal.  t_j itself is sigma^2.  Rows of T are independent of each other,
+// so CTA c keeps rows c, c + P, ... of T.
+//
+// Explicit Q = (I - V T V^T)[I; 0] = E - V K with K = T V_1^T (V_1 the top l x l
+// block of V, unit lower triangular): two more barriers (publish T and V_1,
+// then K), after which every CTA forms its own rows of Q.  When Q is stored in
+// float, that product runs on the FP32 pipe (K and V rounded to float,
+// accumulation in blocks of 8); in FP64 it stays in FP64.
 //
 // Grid barriers spin a bounded number of times; on expiry the kernel sets bit 0
 // of the error flag and every CTA returns (the host reports TT_ERR_TIMEOUT).
@@ -34,7 +40,6 @@ namespace ttsg {
 namespace {
 
 constexpr int QR_THREADS = 256;
-constexpr int QB = 8;                        // reflectors per Q-formation block
 constexpr int NREP = 8;                      // replicas of every reduction slot
 constexpr long long SPIN_LIMIT = 1ll << 24;  // bounded spin (well under a second)
 
@@ -46,15 +51,17 @@ struct QRArgs {
   int q_f64;
   int64_t ldq;
   double* R;
-  double* acc;     // [l][l + 4] factorisation slots (zeroed)
-  double* nrm;     // [l] exact column norms (zeroed)
-  double* pub;     // [2 (l + 1)] values published by the owner of a row
-  double* vtv;     // [nblk][QB][QB] block-diagonal part of V^T V (zeroed)
-  double* accq;    // [nblk][QB][l] Q-formation slots (zeroed)
-  unsigned* bar;   // [0] arrivals, [1] generation
+  double* acc;     // [l][NREP][l] per-step sums (zeroed)
+  double* pub;     // [l][l] row j as published at step j
+  double* Tg;      // [l][l] compact-WY factor T
+  double* V1g;     // [l][l] V_1 (unit lower triangular)
+  double* Kg;      // [l][l] K = T V_1^T
+  unsigned* bar;   // [0] arrivals
   int* err;
   int rows;        // rows per CTA
   int ldy;         // shared-memory row stride (l + 1)
+  int nown;        // rows of T per CTA
+  int cw;          // Q-formation column chunk
 };
 
 __device__ __forceinline__ double warp_sum(double v) {
@@ -92,164 +99,156 @@ __device__ bool grid_barrier(unsigned* bar, unsigned& target, int* err) {
   return fail == 0;
 }
 
-__device__ __forceinline__ int64_t imin64(int64_t a, int64_t b) { return a < b ? a : b; }
-__device__ __forceinline__ int64_t imax64(int64_t a, int64_t b) { return a > b ? a : b; }
 
-// Block-wide sum; every thread gets the result.
-__device__ double block_sum(double v, double* red) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  v = warp_sum(v);
-  __syncthreads();
-  if (lane == 0) red[warp] = v;
-  __syncthreads();
-  double t = 0.0;
-#pragma unroll
-  for (int w = 0; w < QR_THREADS / 32; ++w) t += red[w];
-  return t;
+__device__ __forceinline__ int imin(int a, int b) { return a < b ? a : b; }
+
+// Rows of Q owned by this CTA: Q[g][x] = delta(g, x) - sum_q V[g][q] K[q][x],
+// with V[g][q] = Vr[li][q] for q < g, 1 for q == g, 0 above.
+template <typename E>
+__device__ void form_q(const QRArgs& a, const E* Vr, int ldv, E* Kc, int nloc, int64_t r0) {
+  const int l = (int)a.l, cw = a.cw, tid = threadIdx.x;
+  const int G = QR_THREADS / cw;
+  const int x = tid % cw, rg = tid / cw;
+  for (int c0 = 0; c0 < l; c0 += cw) {
+    const int w = imin(cw, l - c0);
+    __syncthreads();
+    for (int e = tid; e < l * w; e += QR_THREADS) {
+      const int q = e / w, xx = e % w;
+      Kc[q * cw + xx] = (E)__ldcg(a.Kg + (size_t)q * l + c0 + xx);
+    }
+    __syncthreads();
+    if (x >= w) continue;
+    const int col = c0 + x;
+    for (int li = rg; li < nloc; li += G) {
+      const int64_t gi = r0 + li;
+      const int qn = gi < l ? (int)gi : l;
+      const E* vr = Vr + (size_t)li * ldv;
+      E s = 0;
+      for (int q0 = 0; q0 < qn; q0 += 8) {
+        E t = 0;
+        const int q1 = imin(q0 + 8, qn);
+        for (int q = q0; q < q1; ++q) t = fma(vr[q], Kc[q * cw + x], t);
+        s += t;
+      }
+      if (gi < l) s += Kc[gi * cw + x];
+      const E qv = (gi == col ? (E)1 : (E)0) - s;
+      const int64_t dst = gi * a.ldq + col;
+      if (a.q_f64) ((double*)a.Q)[dst] = (double)qv;
+      else ((float*)a.Q)[dst] = (float)qv;
+    }
+  }
 }
 
 __global__ void __launch_bounds__(QR_THREADS) qr_coop_kernel(const QRArgs a) {
   extern __shared__ double smem[];
-  const int l = (int)a.l, ldy = a.ldy, L4 = l + 4;
-  double* Yl = smem;                             // [rows][ldy]: R above, v below the diagonal
-  double* Ql = Yl + (size_t)a.rows * ldy;        // [rows][ldy]: explicit Q rows
-  double* wv = Ql + (a.Q ? (size_t)a.rows * ldy : 0);  // [l + 4]
-  double* tau = wv + L4;                         // [l]
-  double* Tb = tau + l;                          // [QB][QB]
-  double* Wb = Tb + QB * QB;                     // [QB][l]
-  double* Vb = Wb + QB * l;                      // [QB][rows]
-  __shared__ double red[QR_THREADS / 32];
-  __shared__ double sc[8];
+  const int l = (int)a.l, ldy = a.ldy;
+  const int P = gridDim.x, c = blockIdx.x, tid = threadIdx.x;
+  const int warp = tid >> 5, lane = tid & 31;
+  const bool want_q = a.Q != nullptr;
+  const int RP = l >= QR_THREADS ? 1 : QR_THREADS / l;   // row phases of the partial sums
+  double* Yl = smem;                                     // [rows][ldy]: R above, v below
+  double* ts = Yl + (size_t)a.rows * ldy;                // [l] reduced sums t_c
+  double* rj = ts + l;                                   // [l] published row j
+  double* uu = rj + l;                                   // [l] u_c (tau u_c for c > j)
+  double* part = uu + l;                                 // [RP][l]
+  double* Tl = part + (size_t)RP * l;                    // [nown][l] owned rows of T
+  unsigned char* qx = (unsigned char*)(Tl + (size_t)a.nown * l);  // Q-formation region
 
-  const int c = blockIdx.x;
   unsigned btarget = 0;  // running grid-barrier target (used by thread 0)
   const int64_t r0 = (int64_t)c * a.rows;
   const int64_t r1 = a.m < r0 + a.rows ? a.m : r0 + a.rows;
   const int nloc = r1 > r0 ? (int)(r1 - r0) : 0;
-  const int tid = threadIdx.x;
 
   for (int e = tid; e < nloc * l; e += QR_THREADS) {
     const int li = e / l, j = e % l;
     const int64_t src = (r0 + li) * a.sr + (int64_t)j * a.sc;
     Yl[li * ldy + j] = a.y_f64 ? ((const double*)a.Y)[src] : (double)((const float*)a.Y)[src];
   }
+  for (int e = tid; e < a.nown * l; e += QR_THREADS) Tl[e] = 0.0;
   __syncthreads();
-  // v_i of reflector j at local row li (1 on the diagonal, 0 above)
-  auto vval = [&](int li, int j) -> double {
-    const int64_t gi = r0 + li;
-    return gi < j ? 0.0 : (gi == j ? 1.0 : Yl[li * ldy + j]);
-  };
 
-  // ------------------------------------------------ exact norm of column 0
-  {
-    double s = 0.0;
-    for (int li = tid; li < nloc; li += QR_THREADS)
-      if (r0 + li > 0) { const double v = Yl[li * ldy]; s += v * v; }
-    s = block_sum(s, red);
-    if (tid == 0) {
-      if (s != 0.0) atomicAdd(a.nrm, s);
-      if (r0 == 0 && nloc > 0) a.pub[0] = Yl[0];
-    }
-    if (!grid_barrier(a.bar, btarget, a.err)) return;
-    if (tid == 0) { sc[0] = __ldcg(a.nrm); sc[1] = __ldcg(a.pub); }
-    __syncthreads();
-  }
-  double sigma2 = sc[0], alpha = sc[1];
-
-  // ------------------------------------------------------------ factorise
   for (int j = 0; j < l; ++j) {
-    double t = 0.0, beta = alpha, scale = 0.0;
-    if (sigma2 > 0.0) {
-      beta = -copysign(sqrt(alpha * alpha + sigma2), alpha);
-      t = (beta - alpha) / beta;
-      scale = 1.0 / (alpha - beta);
+    const int64_t jl = (int64_t)j - r0;                     // local index of row j
+    const int lb = (int)(jl + 1 < 0 ? 0 : (jl + 1 > nloc ? nloc : jl + 1));  // first row > j
+    const int c_lo = want_q ? 0 : j;
+    // (a) partial sums over the local rows r > j
+    if (lb < nloc) {
+      for (int e = tid; e < RP * l; e += QR_THREADS) {
+        const int col = e % l, rp = e / l;
+        double s = 0.0;
+        if (col >= c_lo)
+          for (int li = lb + rp; li < nloc; li += RP) s = fma(Yl[li * ldy + j], Yl[li * ldy + col], s);
+        part[rp * l + col] = s;
+      }
+      __syncthreads();
+      double* slot = a.acc + ((size_t)j * NREP + (c % NREP)) * l;
+      for (int col = c_lo + tid; col < l; col += QR_THREADS) {
+        double s = part[col];
+        for (int rp = 1; rp < RP; ++rp) s += part[rp * l + col];
+        if (s != 0.0) atomicAdd(slot + col, s);
+      }
+    }
+    if (jl >= 0 && jl < nloc)
+      for (int col = tid; col < l; col += QR_THREADS) a.pub[(size_t)j * l + col] = Yl[jl * ldy + col];
+    if (!grid_barrier(a.bar, btarget, a.err)) return;
+    // (b) the reduced sums and row j
+    for (int col = tid; col < l; col += QR_THREADS) {
+      double s = 0.0;
+      if (col >= c_lo) {
+#pragma unroll
+        for (int q = 0; q < NREP; ++q) s += __ldcg(a.acc + ((size_t)j * NREP + q) * l + col);
+      }
+      ts[col] = s;
+      rj[col] = __ldcg(a.pub + (size_t)j * l + col);
+    }
+    __syncthreads();
+    const double y0 = rj[j], sig2 = ts[j];
+    double beta = y0, tau = 0.0, scale = 0.0;
+    if (sig2 > 0.0) {
+      beta = -copysign(sqrt(fma(y0, y0, sig2)), y0);
+      tau = (beta - y0) / beta;
+      scale = 1.0 / (y0 - beta);
+    }
+    for (int col = c_lo + tid; col < l; col += QR_THREADS) {
+      const double u = fma(scale, ts[col], rj[col]);
+      uu[col] = col > j ? tau * u : u;
     }
     for (int li = tid; li < nloc; li += QR_THREADS) {
       const int64_t gi = r0 + li;
       if (gi > j) Yl[li * ldy + j] *= scale;
       else if (gi == j) Yl[li * ldy + j] = beta;
     }
-    if (tid == 0) tau[j] = t;
     __syncthreads();
-    if (j + 1 >= l) break;
-    double* slot = a.acc + ((size_t)(c % NREP) * l + j) * L4;  // this CTA's replica
-    // local rows holding v_j: the diagonal row (v = 1) and the rows below it
-    const int64_t jl = (int64_t)j - r0;
-    const int ldiag = (jl >= 0 && jl < nloc) ? (int)jl : -1;
-    const int lbeg = jl + 1 > 0 ? (int)imin64(jl + 1, nloc) : 0;
-    // partial products w[col] = sum_{i >= j} v_i Y[i, col], one thread per column
-    for (int col = j + 1 + tid; col < l; col += QR_THREADS) {
-      double p = ldiag >= 0 ? Yl[ldiag * ldy + col] : 0.0;
-      for (int li = lbeg; li < nloc; ++li) p = fma(Yl[li * ldy + j], Yl[li * ldy + col], p);
-      atomicAdd(slot + col, p);
-    }
-    // S1, S2, S3 of column j+1 over rows > j+1 (before the update)
-    {
-      double s1 = 0.0, s2 = 0.0, s3 = 0.0;
-      const int lb2 = jl + 2 > 0 ? (int)imin64(jl + 2, nloc) : 0;
-      for (int li = lb2 + tid; li < nloc; li += QR_THREADS) {
-        const double y = Yl[li * ldy + j + 1], v = Yl[li * ldy + j];
-        s1 = fma(y, y, s1); s2 = fma(v, y, s2); s3 = fma(v, v, s3);
-      }
-      s1 = block_sum(s1, red);
-      s2 = block_sum(s2, red);
-      s3 = block_sum(s3, red);
-      if (tid == 0) {
-        atomicAdd(slot + l, s1);
-        atomicAdd(slot + l + 1, s2);
-        atomicAdd(slot + l + 2, s3);
-        const int64_t o = j + 1 - r0;
-        if (o >= 0 && o < nloc) {
-          a.pub[2 * (j + 1)] = Yl[o * ldy + j + 1];
-          a.pub[2 * (j + 1) + 1] = Yl[o * ldy + j];
-        }
-      }
-    }
-    if (!grid_barrier(a.bar, btarget, a.err)) return;
-    for (int col = j + 1 + tid; col < L4; col += QR_THREADS) {
-      double v = 0.0;
-#pragma unroll
-      for (int q = 0; q < NREP; ++q) v += __ldcg(a.acc + ((size_t)q * l + j) * L4 + col);
-      wv[col] = v;
-    }
-    if (tid == 0) { sc[2] = __ldcg(a.pub + 2 * (j + 1)); sc[3] = __ldcg(a.pub + 2 * (j + 1) + 1); }
-    __syncthreads();
-    // update rows >= j: Y[i, col] -= (tau v_i) w[col]
-    for (int col = j + 1 + tid; col < l; col += QR_THREADS) wv[col] *= -t;
-    __syncthreads();
+    // (c) update rows >= j, columns > j: Y[r][c] -= v_r tau u_c
     {
       const int ncols = l - j - 1;
-      const int r_lo = ldiag >= 0 ? ldiag : lbeg;
+      const int r_lo = (jl >= 0 && jl < nloc) ? (int)jl : lb;
       const int nr = nloc - r_lo;
       for (int e = tid; e < nr * ncols; e += QR_THREADS) {
         const int li = r_lo + e / ncols, col = j + 1 + e % ncols;
-        const double v = li == ldiag ? 1.0 : Yl[li * ldy + j];
-        Yl[li * ldy + col] = fma(v, wv[col], Yl[li * ldy + col]);
+        const double v = (r0 + li == j) ? 1.0 : Yl[li * ldy + j];
+        Yl[li * ldy + col] = fma(-v, uu[col], Yl[li * ldy + col]);
       }
     }
-    // wv[j+1] now holds -tau w[j+1]
-    const double mtw = wv[j + 1], S1 = wv[l], S2 = wv[l + 1], S3 = wv[l + 2];
-    alpha = sc[2] + sc[3] * mtw;
-    sigma2 = S1 + 2.0 * mtw * S2 + mtw * mtw * S3;
+    // (d) column j of the owned rows of T
+    if (want_q) {
+      for (int w = warp; w < a.nown; w += QR_THREADS / 32) {
+        const int i = c + P * w;
+        if (i > j) continue;
+        double* Ti = Tl + (size_t)w * l;
+        if (i == j) {
+          if (lane == 0) Ti[j] = tau;
+          continue;
+        }
+        double s = 0.0;
+        for (int q = i + lane; q < j; q += 32) s = fma(Ti[q], uu[q], s);
+        s = warp_sum(s);
+        if (lane == 0) Ti[j] = -tau * s;
+      }
+    }
     __syncthreads();
-    if (!(sigma2 >= 0.01 * S1)) {
-      // possible cancellation: recompute the norm of the updated column exactly
-      double s = 0.0;
-      const int lb2 = jl + 2 > 0 ? (int)imin64(jl + 2, nloc) : 0;
-      for (int li = lb2 + tid; li < nloc; li += QR_THREADS) {
-        const double v = Yl[li * ldy + j + 1];
-        s = fma(v, v, s);
-      }
-      s = block_sum(s, red);
-      if (tid == 0) atomicAdd(a.nrm + j + 1, s);
-      if (!grid_barrier(a.bar, btarget, a.err)) return;
-      if (tid == 0) sc[4] = __ldcg(a.nrm + j + 1);
-      __syncthreads();
-      sigma2 = sc[4];
-    }
   }
 
-  // ------------------------------------------------------------ R factor
   if (a.R) {
     for (int e = tid; e < nloc * l; e += QR_THREADS) {
       const int li = e / l, col = e % l;
@@ -257,103 +256,47 @@ __global__ void __launch_bounds__(QR_THREADS) qr_coop_kernel(const QRArgs a) {
       if (gi < l) a.R[gi * l + col] = col >= gi ? Yl[li * ldy + col] : 0.0;
     }
   }
-  if (!a.Q) return;
+  if (!want_q) return;
 
   // ------------------------------------------------------------ explicit Q
-  const int nblk = (l + QB - 1) / QB;
-  // block-diagonal part of V^T V, one thread per (block, p, q) with p <= q
-  for (int e = tid; e < nblk * QB * QB; e += QR_THREADS) {
-    const int bi = e / (QB * QB), p = (e / QB) % QB, q = e % QB;
-    const int jp = bi * QB + p, jq = bi * QB + q;
-    if (q < p || jq >= l) continue;
-    double s = 0.0;
-    for (int li = 0; li < nloc; ++li) s += vval(li, jp) * vval(li, jq);
-    if (s != 0.0) atomicAdd(a.vtv + e, s);
+  for (int w = 0; w < a.nown; ++w) {
+    const int i = c + P * w;
+    if (i >= l) break;
+    for (int col = tid; col < l; col += QR_THREADS) a.Tg[(size_t)i * l + col] = Tl[w * l + col];
   }
   for (int e = tid; e < nloc * l; e += QR_THREADS) {
     const int li = e / l, col = e % l;
-    Ql[li * ldy + col] = (r0 + li == col) ? 1.0 : 0.0;
+    const int64_t gi = r0 + li;
+    if (gi < l) a.V1g[gi * l + col] = col < gi ? Yl[li * ldy + col] : (col == gi ? 1.0 : 0.0);
   }
   if (!grid_barrier(a.bar, btarget, a.err)) return;
-  for (int bi = nblk - 1; bi >= 0; --bi) {
-    const int j0 = bi * QB, kb = min(QB, l - j0);
-    if (tid == 0) {
-      // forward recurrence: T[i][i] = tau_i, T[r][i] = -tau_i sum_{q=r}^{i-1} T[r][q] v_q^T v_i
-      const double* G = a.vtv + (size_t)bi * QB * QB;
-      for (int i = 0; i < kb; ++i) {
-        const double ti = tau[j0 + i];
-        for (int r = 0; r < i; ++r) {
-          double s = 0.0;
-          for (int q = r; q < i; ++q) s += Tb[r * QB + q] * __ldcg(G + q * QB + i);
-          Tb[r * QB + i] = -ti * s;
-        }
-        Tb[i * QB + i] = ti;
-        for (int r = i + 1; r < QB; ++r) Tb[r * QB + i] = 0.0;
-      }
-    }
-    // stage v of the block's reflectors (unit diagonal, zeros above) in Vb
-    for (int e = tid; e < QB * nloc; e += QR_THREADS) {
-      const int r = e / nloc, li = e % nloc;
-      Vb[e] = r < kb ? vval(li, j0 + r) : 0.0;
-    }
-    __syncthreads();
-    // W = V_b^T Q over the local rows, columns j0..l-1
-    const int nblk_all = (l + QB - 1) / QB;
-    double* slot = a.accq + ((size_t)(c % NREP) * nblk_all + bi) * QB * l;
-    const int ncols = l - j0;
-    const int vlo = (int)imax64(0, imin64((int64_t)j0 - r0, nloc));
-    for (int e = tid; e < kb * ncols; e += QR_THREADS) {
-      const int r = e / ncols, col = j0 + e % ncols;
-      double s = 0.0;
-      for (int li = vlo; li < nloc; ++li) s = fma(Vb[r * nloc + li], Ql[li * ldy + col], s);
-      atomicAdd(slot + (size_t)r * l + col, s);
-    }
-    if (!grid_barrier(a.bar, btarget, a.err)) return;
-    for (int e = tid; e < QB * l; e += QR_THREADS) {
-      double v = 0.0;
-      if (e < kb * l) {
-#pragma unroll
-        for (int q = 0; q < NREP; ++q)
-          v += __ldcg(a.accq + ((size_t)q * nblk_all + bi) * QB * l + e);
-      }
-      Wb[e] = v;
-    }
-    __syncthreads();
-    // Wb <- T Wb
-    for (int col = j0 + tid; col < l; col += QR_THREADS) {
-      double w[QB];
-#pragma unroll
-      for (int r = 0; r < QB; ++r) w[r] = r < kb ? Wb[r * l + col] : 0.0;
-#pragma unroll
-      for (int r = 0; r < QB; ++r) {
-        double s = 0.0;
-#pragma unroll
-        for (int q = 0; q < QB; ++q) s += (q >= r && q < kb) ? Tb[r * QB + q] * w[q] : 0.0;
-        if (r < kb) Wb[r * l + col] = s;
-      }
-    }
-    __syncthreads();
-    // Q -= V_b (T W)
-    for (int e = tid; e < (nloc - vlo) * ncols; e += QR_THREADS) {
-      const int li = vlo + e / ncols, col = j0 + e % ncols;
-      double s = Ql[li * ldy + col];
-#pragma unroll
-      for (int r = 0; r < QB; ++r) s = fma(-Vb[r * nloc + li], Wb[r * l + col], s);
-      Ql[li * ldy + col] = s;
-    }
-    __syncthreads();
+  // K[i][x] = sum_{q = i}^{x} T[i][q] V_1[x][q] for the owned rows i, one warp per (i, x)
+  for (int task = warp; task < a.nown * l; task += QR_THREADS / 32) {
+    const int w = task / l, x = task % l;
+    const int i = c + P * w;
+    if (i >= l) continue;
+    const double* Ti = Tl + (size_t)w * l;
+    double s = 0.0;
+    for (int q = i + lane; q <= x; q += 32) s = fma(Ti[q], __ldcg(a.V1g + (size_t)x * l + q), s);
+    s = warp_sum(s);
+    if (lane == 0) a.Kg[(size_t)i * l + x] = s;
   }
-  for (int e = tid; e < nloc * l; e += QR_THREADS) {
-    const int li = e / l, col = e % l;
-    const double v = Ql[li * ldy + col];
-    const int64_t dst = (r0 + li) * a.ldq + col;
-    if (a.q_f64) ((double*)a.Q)[dst] = v;
-    else ((float*)a.Q)[dst] = (float)v;
+  if (!grid_barrier(a.bar, btarget, a.err)) return;
+  if (a.q_f64) {
+    form_q<double>(a, Yl, ldy, (double*)qx, nloc, r0);
+  } else {
+    float* Vf = (float*)qx;
+    float* Kc = Vf + (size_t)a.rows * l;
+    for (int e = tid; e < nloc * l; e += QR_THREADS) {
+      const int li = e / l, q = e % l;
+      Vf[li * l + q] = (float)Yl[li * ldy + q];
+    }
+    form_q<float>(a, Vf, l, Kc, nloc, r0);
   }
 }
 
 struct QRPlan {
-  int P, rows, ldy;
+  int P, rows, ldy, nown, cw;
   size_t smem;
 };
 
@@ -368,22 +311,35 @@ int num_sms() {
   return sms;
 }
 
-QRPlan plan(int64_t m, int64_t l, int sms, bool want_q) {
+constexpr size_t QR_SMEM_MAX = 220 * 1024;
+
+QRPlan plan(int64_t m, int64_t l, int sms, bool want_q, bool q_f64) {
   QRPlan p;
   const int64_t min_rows = 16;
   int64_t P = std::min<int64_t>(sms, std::max<int64_t>(1, ceil_div(m, min_rows)));
   p.rows = (int)ceil_div(m, P);
   p.P = (int)ceil_div(m, p.rows);
   p.ldy = (int)l + 1;
-  p.smem = ((size_t)p.rows * p.ldy * (want_q ? 2 : 1) + (l + 4) + l + QB * QB + QB * l +
-            (size_t)QB * p.rows) * sizeof(double);
+  p.nown = (int)ceil_div(l, p.P);
+  const int RP = l >= QR_THREADS ? 1 : QR_THREADS / (int)l;
+  const size_t base = ((size_t)p.rows * p.ldy + 3 * l + (size_t)RP * l + (size_t)p.nown * l) *
+                      sizeof(double);
+  p.cw = 8;
+  p.smem = base;
+  if (want_q) {
+    // widest column chunk (a divisor of the block size) that fits
+    for (int cw : {64, 32, 16, 8}) {
+      p.cw = cw;
+      const size_t qx = q_f64 ? (size_t)l * cw * sizeof(double)
+                              : ((size_t)p.rows * l + (size_t)l * cw) * sizeof(float);
+      p.smem = base + qx;
+      if (p.smem <= QR_SMEM_MAX) break;
+    }
+  }
   return p;
 }
 
-size_t slots_doubles(int64_t l) {
-  const int64_t nblk = (l + QB - 1) / QB;
-  return (size_t)(NREP * l * (l + 4) + l + 2 * (l + 1) + nblk * QB * QB + NREP * nblk * QB * l);
-}
+size_t slots_doubles(int64_t l) { return (size_t)(NREP * l * l + 4 * l * l); }
 
 }  // namespace
 
@@ -398,8 +354,8 @@ void qr_f64(const void* Y, int y_f64, int64_t m, int64_t l, int64_t sr, int64_t 
   if (m < l || l <= 0) throw Error(TT_ERR_ARG, "qr_f64: need m >= l >= 1");
   if (g_dry_run) return;
   const int sms = num_sms();
-  QRPlan p = plan(m, l, sms, Q != nullptr);
-  if (p.smem > 220 * 1024)
+  QRPlan p = plan(m, l, sms, Q != nullptr, q_f64 != 0);
+  if (p.smem > QR_SMEM_MAX)
     throw Error(TT_ERR_UNSUPPORTED, "qr_f64: block of " + std::to_string(p.rows) + " x " +
                                         std::to_string(l) + " does not fit in shared memory");
   Arena ar(ws, ws_bytes);
@@ -408,19 +364,18 @@ void qr_f64(const void* Y, int y_f64, int64_t m, int64_t l, int64_t sr, int64_t 
   QRArgs a;
   a.Y = Y; a.y_f64 = y_f64; a.m = m; a.l = l; a.sr = sr; a.sc = sc;
   a.Q = Q; a.q_f64 = q_f64; a.ldq = ldq; a.R = R;
-  const int64_t nblk = (l + QB - 1) / QB;
   a.acc = slots;
-  a.nrm = a.acc + NREP * l * (l + 4);
-  a.pub = a.nrm + l;
-  a.vtv = a.pub + 2 * (l + 1);
-  a.accq = a.vtv + nblk * QB * QB;
-  a.bar = bar; a.err = err_flag; a.rows = p.rows; a.ldy = p.ldy;
+  a.pub = a.acc + NREP * l * l;
+  a.Tg = a.pub + l * l;
+  a.V1g = a.Tg + l * l;
+  a.Kg = a.V1g + l * l;
+  a.bar = bar; a.err = err_flag; a.rows = p.rows; a.ldy = p.ldy; a.nown = p.nown; a.cw = p.cw;
   TT_CUDA(cudaMemsetAsync(bar, 0, 64 * sizeof(unsigned), st));
-  TT_CUDA(cudaMemsetAsync(slots, 0, sizeof(double) * slots_doubles(l), st));
+  TT_CUDA(cudaMemsetAsync(a.acc, 0, sizeof(double) * NREP * l * l, st));
   static bool attr = false;
   if (!attr) {
     TT_CUDA(cudaFuncSetAttribute(qr_coop_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 220 * 1024));
+                                 (int)QR_SMEM_MAX));
     attr = true;
   }
   void* args[] = {(void*)&a};

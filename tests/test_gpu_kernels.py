@@ -145,7 +145,8 @@ def test_dot_parity(g, mode):
     assert abs(out - ref) <= 10 * tol_of(g, mode) * scale
 
 
-@pytest.mark.parametrize("m,l", [(1, 1), (70, 70), (4736, 74), (300, 17), (64, 64), (9000, 130)])
+@pytest.mark.parametrize("m,l", [(1, 1), (70, 70), (4736, 74), (300, 17), (64, 64), (9000, 130),
+                                 (17664, 138), (40, 33)])
 def test_qr_f64(g, m, l):
     rng = np.random.default_rng(m + l)
     Y = rng.standard_normal((m, l))
