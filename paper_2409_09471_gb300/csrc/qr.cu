@@ -41,6 +41,8 @@ namespace {
 
 constexpr int QR_THREADS = 256;
 constexpr int NREP = 8;                      // replicas of every reduction slot
+constexpr int QR_RPMAX = 4;                  // row phases of the partial sums
+static_assert(NREP == 8, "the replica sums below are written out for 8 replicas");
 constexpr long long SPIN_LIMIT = 1ll << 24;  // bounded spin (well under a second)
 
 struct QRArgs {
@@ -72,8 +74,9 @@ __device__ __forceinline__ double warp_sum(double v) {
 
 // Grid barrier on a monotonic arrival counter (bar[0], zeroed before the
 // launch): barrier number b completes when the counter reaches (b + 1) * P, so
-// each CTA keeps a running target and needs one release fence, one atomic and
-// a poll of the same word; no reset, no second word.  Returns false when the
+// each CTA keeps a running target; thread 0 arrives with a release reduction
+// (ordering the CTA's earlier writes and atomics, which it has observed through
+// the block barrier) and polls with acquire loads.  Returns false when the
 // barrier timed out (bit 0 of the error flag is then set).
 __device__ bool grid_barrier(unsigned* bar, unsigned& target, int* err) {
   __shared__ int fail;
@@ -81,24 +84,22 @@ __device__ bool grid_barrier(unsigned* bar, unsigned& target, int* err) {
   if (threadIdx.x == 0) {
     fail = 0;
     target += gridDim.x;
-    __threadfence();
-    atomicAdd(bar, 1u);
-    volatile unsigned* vc = bar;
+    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(bar), "r"(1u) : "memory");
     long long spins = 0;
-    while ((int)(*vc - target) < 0) {
+    while (true) {
+      unsigned v;
+      asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(bar) : "memory");
+      if ((int)(v - target) >= 0) break;
       if (++spins > SPIN_LIMIT || (*(volatile int*)err & 1)) {
         atomicOr(err, 1);
         fail = 1;
         break;
       }
-      __nanosleep(20);
     }
-    __threadfence();
   }
   __syncthreads();
   return fail == 0;
 }
-
 
 __device__ __forceinline__ int imin(int a, int b) { return a < b ? a : b; }
 
@@ -145,15 +146,21 @@ __global__ void __launch_bounds__(QR_THREADS) qr_coop_kernel(const QRArgs a) {
   const int P = gridDim.x, c = blockIdx.x, tid = threadIdx.x;
   const int warp = tid >> 5, lane = tid & 31;
   const bool want_q = a.Q != nullptr;
-  const int RP = l >= QR_THREADS ? 1 : QR_THREADS / l;   // row phases of the partial sums
+  // float Q: the compact-WY products (columns < j) run on the FP32 pipe from a
+  // float copy of the normalised reflectors (also the V operand of form_q)
+  const bool tf = want_q && !a.q_f64;
   double* Yl = smem;                                     // [rows][ldy]: R above, v below
   double* ts = Yl + (size_t)a.rows * ldy;                // [l] reduced sums t_c
   double* rj = ts + l;                                   // [l] published row j
   double* uu = rj + l;                                   // [l] u_c (tau u_c for c > j)
-  double* part = uu + l;                                 // [RP][l]
-  double* Tl = part + (size_t)RP * l;                    // [nown][l] owned rows of T
-  unsigned char* qx = (unsigned char*)(Tl + (size_t)a.nown * l);  // Q-formation region
-
+  double* part = uu + l;                                 // [QR_RPMAX][l]
+  double* Tl = part + (size_t)QR_RPMAX * l;              // [nown][l] owned rows of T
+  float* partf = (float*)(Tl + (size_t)a.nown * l);      // [QR_RPMAX][l]
+  float* yjf = partf + (size_t)QR_RPMAX * l;             // [rows] column j in float
+  float* Vf = yjf + a.rows;                              // [rows][l] reflectors in float
+  unsigned char* qx =                                    // Q-formation chunk, 16-byte aligned
+      (unsigned char*)(((uintptr_t)(Vf + (tf ? (size_t)a.rows * l : 0)) + 15) & ~(uintptr_t)15);
+  __shared__ double hs[4];  // beta, tau, scale of the current reflector
   unsigned btarget = 0;  // running grid-barrier target (used by thread 0)
   const int64_t r0 = (int64_t)c * a.rows;
   const int64_t r1 = a.m < r0 + a.rows ? a.m : r0 + a.rows;
@@ -166,88 +173,185 @@ __global__ void __launch_bounds__(QR_THREADS) qr_coop_kernel(const QRArgs a) {
   }
   for (int e = tid; e < a.nown * l; e += QR_THREADS) Tl[e] = 0.0;
   __syncthreads();
+  if (tf)
+    for (int li = tid; li < nloc; li += QR_THREADS) yjf[li] = (float)Yl[li * ldy];
+  __syncthreads();
+
+  // column jj of the owned rows of T: T[i][jj] = -tau_jj sum_{q=i}^{jj-1} T[i][q] p_q
+  // with p_q = uu[q] and tau_jj = hs[1] of step jj
+  auto t_column = [&](int jj) {
+    const double tj = hs[1];
+    for (int w = warp; w < a.nown; w += QR_THREADS / 32) {
+      const int i = c + P * w;
+      if (i > jj) continue;
+      double* Ti = Tl + (size_t)w * l;
+      if (i == jj) {
+        if (lane == 0) Ti[jj] = tj;
+        continue;
+      }
+      double s = 0.0;
+      for (int q = i + lane; q < jj; q += 32) s = fma(Ti[q], uu[q], s);
+      s = warp_sum(s);
+      if (lane == 0) Ti[jj] = -tj * s;
+    }
+  };
 
   for (int j = 0; j < l; ++j) {
     const int64_t jl = (int64_t)j - r0;                     // local index of row j
     const int lb = (int)(jl + 1 < 0 ? 0 : (jl + 1 > nloc ? nloc : jl + 1));  // first row > j
-    const int c_lo = want_q ? 0 : j;
+    const int ncol = l - j;                                 // FP64 columns j .. l-1
+    const int RPd = imin(QR_RPMAX, ncol >= QR_THREADS ? 1 : QR_THREADS / ncol);
+    const int RPt = j == 0 ? 1 : imin(QR_RPMAX, j >= QR_THREADS ? 1 : QR_THREADS / j);
     // (a) partial sums over the local rows r > j
     if (lb < nloc) {
-      for (int e = tid; e < RP * l; e += QR_THREADS) {
-        const int col = e % l, rp = e / l;
-        double s = 0.0;
-        if (col >= c_lo)
-          for (int li = lb + rp; li < nloc; li += RP) s = fma(Yl[li * ldy + j], Yl[li * ldy + col], s);
-        part[rp * l + col] = s;
+      for (int e = tid; e < RPd * ncol; e += QR_THREADS) {
+        const int col = j + e % ncol, rp = e / ncol;
+        // two independent chains: dependent FP64 FMAs are slow on this part
+        double s0 = 0.0, s1 = 0.0;
+        int li = lb + rp;
+        for (; li + RPd < nloc; li += 2 * RPd) {
+          s0 = fma(Yl[li * ldy + j], Yl[li * ldy + col], s0);
+          s1 = fma(Yl[(li + RPd) * ldy + j], Yl[(li + RPd) * ldy + col], s1);
+        }
+        if (li < nloc) s0 = fma(Yl[li * ldy + j], Yl[li * ldy + col], s0);
+        part[rp * l + col] = s0 + s1;
+      }
+      if (want_q && j > 0) {
+        for (int e = tid; e < RPt * j; e += QR_THREADS) {
+          const int col = e % j, rp = e / j;
+          if (tf) {
+            float s = 0.f;
+            for (int li = lb + rp; li < nloc; li += RPt) s = fmaf(yjf[li], Vf[li * l + col], s);
+            partf[rp * l + col] = s;
+          } else {
+            double s0 = 0.0, s1 = 0.0;
+            int li = lb + rp;
+            for (; li + RPt < nloc; li += 2 * RPt) {
+              s0 = fma(Yl[li * ldy + j], Yl[li * ldy + col], s0);
+              s1 = fma(Yl[(li + RPt) * ldy + j], Yl[(li + RPt) * ldy + col], s1);
+            }
+            if (li < nloc) s0 = fma(Yl[li * ldy + j], Yl[li * ldy + col], s0);
+            part[rp * l + col] = s0 + s1;
+          }
+        }
       }
       __syncthreads();
       double* slot = a.acc + ((size_t)j * NREP + (c % NREP)) * l;
-      for (int col = c_lo + tid; col < l; col += QR_THREADS) {
-        double s = part[col];
-        for (int rp = 1; rp < RP; ++rp) s += part[rp * l + col];
-        if (s != 0.0) atomicAdd(slot + col, s);
+      for (int col = (want_q ? 0 : j) + tid; col < l; col += QR_THREADS) {
+        double s;
+        if (col >= j) {
+          s = part[col];
+          for (int rp = 1; rp < RPd; ++rp) s += part[rp * l + col];
+        } else if (tf) {
+          float f = partf[col];
+          for (int rp = 1; rp < RPt; ++rp) f += partf[rp * l + col];
+          s = (double)f;
+        } else {
+          s = part[col];
+          for (int rp = 1; rp < RPt; ++rp) s += part[rp * l + col];
+        }
+        if (__double_as_longlong(s) != 0) atomicAdd(slot + col, s);
       }
     }
+    // column j-1 of T while the other CTAs catch up (uu and tau still hold step j-1)
+    if (want_q && j > 0) t_column(j - 1);
     if (jl >= 0 && jl < nloc)
       for (int col = tid; col < l; col += QR_THREADS) a.pub[(size_t)j * l + col] = Yl[jl * ldy + col];
     if (!grid_barrier(a.bar, btarget, a.err)) return;
-    // (b) the reduced sums and row j
-    for (int col = tid; col < l; col += QR_THREADS) {
-      double s = 0.0;
-      if (col >= c_lo) {
+    // (b) the reduced sums and row j; lane 0 of warp 0 meanwhile forms the
+    // reflector's scalars from x = alpha^2 + sigma^2 with one reciprocal square
+    // root and one reciprocal: beta = -sign(alpha) sqrt(x), tau = (beta -
+    // alpha) / beta = 1 + |alpha| / sqrt(x), scale = 1 / (alpha - beta)
+    const int c_lo = want_q ? 0 : j;
+    if (warp == 0) {
+      if (lane == 0) {
+        double v[NREP];
 #pragma unroll
-        for (int q = 0; q < NREP; ++q) s += __ldcg(a.acc + ((size_t)j * NREP + q) * l + col);
+        for (int q = 0; q < NREP; ++q) v[q] = __ldcg(a.acc + ((size_t)j * NREP + q) * l + j);
+        const double y0 = __ldcg(a.pub + (size_t)j * l + j);
+        const double sig2 = ((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + (v[6] + v[7]));
+        double beta = y0, tau = 0.0, scale = 0.0;
+        if (sig2 > 0.0) {
+          const double x = fma(y0, y0, sig2);
+          const double rs = rsqrt(x);
+          beta = -copysign(x * rs, y0);
+          tau = fma(fabs(y0), rs, 1.0);
+          scale = 1.0 / (y0 - beta);
+        }
+        hs[0] = beta; hs[1] = tau; hs[2] = scale;
       }
-      ts[col] = s;
-      rj[col] = __ldcg(a.pub + (size_t)j * l + col);
+    } else {
+      for (int col = tid - 32; col < l; col += QR_THREADS - 32) {
+        double s = 0.0;
+        if (col >= c_lo) {
+          double v[NREP];
+#pragma unroll
+          for (int q = 0; q < NREP; ++q) v[q] = __ldcg(a.acc + ((size_t)j * NREP + q) * l + col);
+          s = ((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + (v[6] + v[7]));
+        }
+        ts[col] = s;
+        rj[col] = __ldcg(a.pub + (size_t)j * l + col);
+      }
     }
     __syncthreads();
-    const double y0 = rj[j], sig2 = ts[j];
-    double beta = y0, tau = 0.0, scale = 0.0;
-    if (sig2 > 0.0) {
-      beta = -copysign(sqrt(fma(y0, y0, sig2)), y0);
-      tau = (beta - y0) / beta;
-      scale = 1.0 / (y0 - beta);
-    }
+    const double beta = hs[0], tau = hs[1], scale = hs[2];
     for (int col = c_lo + tid; col < l; col += QR_THREADS) {
       const double u = fma(scale, ts[col], rj[col]);
       uu[col] = col > j ? tau * u : u;
     }
     for (int li = tid; li < nloc; li += QR_THREADS) {
       const int64_t gi = r0 + li;
-      if (gi > j) Yl[li * ldy + j] *= scale;
-      else if (gi == j) Yl[li * ldy + j] = beta;
+      if (gi > j) {
+        const double v = Yl[li * ldy + j] * scale;
+        Yl[li * ldy + j] = v;
+        if (tf) Vf[li * l + j] = (float)v;
+      } else if (gi == j) {
+        Yl[li * ldy + j] = beta;
+      }
     }
     __syncthreads();
-    // (c) update rows >= j, columns > j: Y[r][c] -= v_r tau u_c
+    // (c) update rows >= j, columns > j: Y[r][c] -= v_r tau u_c (column j+1
+    // also refreshes its float copy for the next step)
     {
       const int ncols = l - j - 1;
       const int r_lo = (jl >= 0 && jl < nloc) ? (int)jl : lb;
-      const int nr = nloc - r_lo;
-      for (int e = tid; e < nr * ncols; e += QR_THREADS) {
-        const int li = r_lo + e / ncols, col = j + 1 + e % ncols;
-        const double v = (r0 + li == j) ? 1.0 : Yl[li * ldy + j];
-        Yl[li * ldy + col] = fma(-v, uu[col], Yl[li * ldy + col]);
-      }
-    }
-    // (d) column j of the owned rows of T
-    if (want_q) {
-      for (int w = warp; w < a.nown; w += QR_THREADS / 32) {
-        const int i = c + P * w;
-        if (i > j) continue;
-        double* Ti = Tl + (size_t)w * l;
-        if (i == j) {
-          if (lane == 0) Ti[j] = tau;
-          continue;
+      if (ncols > 0 && r_lo < nloc) {
+        const int RPu = ncols >= QR_THREADS ? 1 : QR_THREADS / ncols;
+        for (int e = tid; e < RPu * ncols; e += QR_THREADS) {
+          const int col = j + 1 + e % ncols, rp = e / ncols;
+          const double w = uu[col];
+          const bool fj = tf && col == j + 1;
+          int li = r_lo + rp;
+          // four rows at a time, loads before the FMAs
+          for (; li + 3 * RPu < nloc; li += 4 * RPu) {
+            double v[4], y[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+              const int lk = li + k * RPu;
+              v[k] = (r0 + lk == j) ? 1.0 : Yl[lk * ldy + j];
+              y[k] = Yl[lk * ldy + col];
+            }
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+              const int lk = li + k * RPu;
+              y[k] = fma(-v[k], w, y[k]);
+              Yl[lk * ldy + col] = y[k];
+              if (fj) yjf[lk] = (float)y[k];
+            }
+          }
+          for (; li < nloc; li += RPu) {
+            const double v = (r0 + li == j) ? 1.0 : Yl[li * ldy + j];
+            const double y = fma(-v, w, Yl[li * ldy + col]);
+            Yl[li * ldy + col] = y;
+            if (fj) yjf[li] = (float)y;
+          }
         }
-        double s = 0.0;
-        for (int q = i + lane; q < j; q += 32) s = fma(Ti[q], uu[q], s);
-        s = warp_sum(s);
-        if (lane == 0) Ti[j] = -tau * s;
       }
     }
     __syncthreads();
   }
+  if (want_q) t_column(l - 1);
+  __syncthreads();
 
   if (a.R) {
     for (int e = tid; e < nloc * l; e += QR_THREADS) {
@@ -285,13 +389,7 @@ __global__ void __launch_bounds__(QR_THREADS) qr_coop_kernel(const QRArgs a) {
   if (a.q_f64) {
     form_q<double>(a, Yl, ldy, (double*)qx, nloc, r0);
   } else {
-    float* Vf = (float*)qx;
-    float* Kc = Vf + (size_t)a.rows * l;
-    for (int e = tid; e < nloc * l; e += QR_THREADS) {
-      const int li = e / l, q = e % l;
-      Vf[li * l + q] = (float)Yl[li * ldy + q];
-    }
-    form_q<float>(a, Vf, l, Kc, nloc, r0);
+    form_q<float>(a, Vf, l, (float*)qx, nloc, r0);
   }
 }
 
@@ -321,18 +419,18 @@ QRPlan plan(int64_t m, int64_t l, int sms, bool want_q, bool q_f64) {
   p.P = (int)ceil_div(m, p.rows);
   p.ldy = (int)l + 1;
   p.nown = (int)ceil_div(l, p.P);
-  const int RP = l >= QR_THREADS ? 1 : QR_THREADS / (int)l;
-  const size_t base = ((size_t)p.rows * p.ldy + 3 * l + (size_t)RP * l + (size_t)p.nown * l) *
-                      sizeof(double);
+  const bool tf = want_q && !q_f64;
+  const size_t base = ((size_t)p.rows * p.ldy + 3 * l + (size_t)QR_RPMAX * l + (size_t)p.nown * l) *
+                          sizeof(double) +
+                      ((size_t)QR_RPMAX * l + p.rows + (tf ? (size_t)p.rows * l : 0)) * sizeof(float) +
+                      16;
   p.cw = 8;
   p.smem = base;
   if (want_q) {
     // widest column chunk (a divisor of the block size) that fits
     for (int cw : {64, 32, 16, 8}) {
       p.cw = cw;
-      const size_t qx = q_f64 ? (size_t)l * cw * sizeof(double)
-                              : ((size_t)p.rows * l + (size_t)l * cw) * sizeof(float);
-      p.smem = base + qx;
+      p.smem = base + (size_t)l * cw * (q_f64 ? sizeof(double) : sizeof(float));
       if (p.smem <= QR_SMEM_MAX) break;
     }
   }
