@@ -46,6 +46,10 @@ FP64_ALU_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 FP32_ALU_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 # TF32 dense tensor peak = measured BF16 peak x nominal TF32/BF16 ratio (1.1 / 2.25)
 TF32_OVER_BF16 = 1.1 / 2.25
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the
+# dominant kernel at this workload, from one ncu capture of the current kernel
+# (None once the kernel changes and until it is captured again)
+TRAFFIC_BYTES = {"qr_f64": 1.833216e6}
 
 
 def parse():
@@ -314,7 +318,7 @@ def run_ours(args):
         roof = {"bound": "hbm", "achieved": by_per / (avg_ms * 1e-3) / 1e9, "peak": pk["hbm_gbs"],
                 "unit": "GB/s", "peak_kind": f"{pk_kind} copy bandwidth"}
     roof["frac"] = roof["achieved"] / roof["peak"]
-    roof["traffic"] = None
+    roof["traffic"] = TRAFFIC_BYTES.get(dom)
     roof["kernel"] = dom
     roof["launches_per_step"] = nl.value / args.steps
     roof["avg_launch_us"] = avg_ms * 1e3
