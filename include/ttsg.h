@@ -169,6 +169,56 @@ size_t tt_round_rand_workspace(int mode, int nterms, const tt_vec* terms, int64_
                                int64_t oversample);
 
 /*
+ * Backward contractions of the adjoint gradient.  The paper solves A x = b
+ * only; these differentiate its inner-product sweep (Sec. 2.2) so that the
+ * loss ||x - x_t||^2 can be differentiated through an adjoint solve
+ * A^T lambda = 2 (x - x_t) (Alg. 4 applied to A^T):
+ *   dL/dtheta_k = -<lambda, (dA/dtheta_k) x>,  dL/db = lambda.
+ *
+ * tt_dot_grad - derivative of <x, y> with respect to every core of y:
+ *   g_k[b, i, c] = sum_{a, a'} P_k[a, b] X_k[a, i, a'] Q_{k+1}[a', c],
+ * where P_k (x.rank[k] x y.rank[k]) and Q_{k+1} are the left and right
+ * interface matrices of x against y (P_0 = Q_d = 1).
+ * g (host array of d device pointers): output core k has y's core-k shape
+ * [y.rank[k]][n_k][y.rank[k+1]], in the mode's precision; the caller owns it.
+ * Errors: TT_ERR_ARG for mismatched d or mode sizes, null pointers.
+ */
+int tt_dot_grad(int mode, const tt_vec* x, const tt_vec* y, void* const* g, void* ws,
+                size_t ws_bytes, void* stream);
+size_t tt_dot_grad_workspace(int mode, const tt_vec* x, const tt_vec* y);
+
+/*
+ * tt_local_dots - out[k] = <x, (I x .. x M_k x .. x I) y> for k = 0..d-1
+ * (M_k acting on mode k), i.e. <g_k, M_k x_2 Y_k> with g_k as in tt_dot_grad.
+ * With M_k the 1-D operator of term k this is the theta-gradient of the loss
+ * up to sign.  M (host array of d device pointers): n_k x n_k row-major
+ * matrices in the mode's precision (entries may repeat).  out (device,
+ * double[d]), accumulated in FP64.
+ */
+int tt_local_dots(int mode, const tt_vec* x, const tt_vec* y, void* const* M, double* out,
+                  void* ws, size_t ws_bytes, void* stream);
+size_t tt_local_dots_workspace(int mode, const tt_vec* x, const tt_vec* y);
+
+/*
+ * tt_kron_sum_op - cores of the rank-2 TT operator
+ *   A(theta) = sum_k theta_k (I x .. x M_k x .. x I)
+ * (first core [theta_1 M_1, I], middle [[I, 0], [theta_k M_k, I]], last
+ * [I; theta_d M_d]; d == 1 gives theta_1 M_1).  n (host, d), M (host array of
+ * d device pointers to n_k x n_k row-major matrices), theta (host, d; NULL =
+ * all ones), cores (host array of d device pointers; core k holds
+ * R_{k-1} n_k n_k R_k elements with R = 1, 2, .., 2, 1).
+ */
+int tt_kron_sum_op(int mode, int d, const int64_t* n, void* const* M, const double* theta,
+                   void* const* cores, void* stream);
+
+/*
+ * tt_op_transpose - cores of A^T: out core k [R_{k-1}][n][n][R_k] with the
+ * output and input mode indices of A's core k swapped.  cores: host array of d
+ * device pointers, each sized like A's core k; must not alias A's cores.
+ */
+int tt_op_transpose(int mode, const tt_op* A, void* const* cores, void* stream);
+
+/*
  * tt_gaussian - fill out (device, ``count`` elements: double for TT_MODE_FP64,
  * float otherwise) with std times element e of the Gaussian stream (seed,
  * stream_id): Philox4x32-10 (Salmon et al., SC'11) with counter (lo(e/2),

@@ -46,3 +46,35 @@ def loss_and_grads(theta, L, b_cores, xt_cores):
         Lam = lam.reshape(left.shape[0], ns[k], right.shape[0])
         dcores.append(np.einsum("xiy,xa,yc->aic", Lam, left, right))
     return loss, dtheta, dcores, x, lam
+
+
+def interfaces(x, y):
+    """Left and right interface matrices of TT ``x`` against TT ``y``
+    (Section 2.2 inner-product sweep, kept at every bond):
+    ``P[0] = 1``, ``P[k+1] = sum_i X_k[:, i, :]^T P[k] Y_k[:, i, :]`` and
+    ``Q[d] = 1``, ``Q[k] = sum_i X_k[:, i, :] Q[k+1] Y_k[:, i, :]^T``."""
+    d = len(x)
+    P = [None] * (d + 1)
+    Q = [None] * (d + 1)
+    P[0] = np.ones((1, 1))
+    for k in range(d):
+        P[k + 1] = sum(x[k][:, i, :].T @ P[k] @ y[k][:, i, :] for i in range(x[k].shape[1]))
+    Q[d] = np.ones((1, 1))
+    for k in range(d - 1, -1, -1):
+        Q[k] = sum(x[k][:, i, :] @ Q[k + 1] @ y[k][:, i, :].T for i in range(x[k].shape[1]))
+    return P, Q
+
+
+def dot_grad(x, y):
+    """Derivative of ``<x, y>`` with respect to every core of ``y``:
+    ``G_k[b, i, c] = sum_{a, a'} P_k[a, b] X_k[a, i, a'] Q_{k+1}[a', c]``."""
+    P, Q = interfaces(x, y)
+    return [np.einsum("ab,aic,ce->bie", P[k], x[k], Q[k + 1]) for k in range(len(x))]
+
+
+def local_dots(x, y, mats):
+    """``out[k] = <x, (I x .. x mats[k] x .. x I) y>`` through the interfaces:
+    ``<G_k, mats[k] x_2 Y_k>``."""
+    G = dot_grad(x, y)
+    return np.array([np.sum(G[k] * np.einsum("ij,bjc->bic", mats[k], y[k]))
+                     for k in range(len(x))])

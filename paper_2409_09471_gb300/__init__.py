@@ -5,7 +5,10 @@ library behind the C ABI declared in ``include/ttsg.h``.  PyTorch provides
 device memory and the current CUDA stream.  The functions keep the C names:
 
 ``tt_matvec``, ``tt_sketch``, ``tt_dot``, ``tt_round_rand``, ``tt_gaussian``,
-``tt_qr_f64``, ``tt_lstsq_f64``, ``tt_sgmres_solve``.
+``tt_qr_f64``, ``tt_lstsq_f64``, ``tt_sgmres_solve``, and the adjoint helpers
+``tt_dot_grad``, ``tt_local_dots``, ``tt_kron_sum_op``, ``tt_op_transpose``.
+:func:`solve_loss` is a ``torch.autograd.Function`` over the solve whose
+backward pass is the adjoint solve plus those backward contractions.
 
 TT vectors are :class:`TT` objects (a list of contiguous CUDA tensors with
 shapes ``[r_{k-1}, n_k, r_k]``); TT operators are lists of contiguous CUDA
@@ -25,7 +28,8 @@ from ._abi import (lib, TTVec, TTVecOut, TTOp, SolverParams, SolverInfo, MODE_FP
 
 __all__ = ["TT", "tt_matvec", "tt_sketch", "tt_dot", "tt_round_rand", "tt_gaussian", "tt_qr_f64",
            "tt_lstsq_f64", "tt_sgmres_solve", "MODE_FP64", "MODE_FP32", "MODE_TF32", "TTError",
-           "LIB_PATH", "mode_dtype", "op_to_device"]
+           "LIB_PATH", "mode_dtype", "op_to_device", "tt_dot_grad", "tt_local_dots",
+           "tt_kron_sum_op", "tt_op_transpose", "solve_loss"]
 
 
 def mode_dtype(mode: int) -> torch.dtype:
@@ -272,3 +276,134 @@ def tt_sgmres_solve(op, b: TT, maxit: int, tol: float, rmax: int, mode: int = MO
                svd_nonconverged=info.svd_nonconverged,
                workspace_bytes=int(need))
     return x, out
+
+
+# ------------------------------------------------------------------ adjoint
+def tt_dot_grad(x: TT, y: TT, mode: int = MODE_FP64, stream=None) -> List[torch.Tensor]:
+    """Derivative of ``<x, y>`` with respect to every core of ``y`` (cores
+    shaped like y's)."""
+    _check_dtype(x.cores + y.cores, mode)
+    g = [torch.empty_like(c) for c in y.cores]
+    xd, k1 = x._desc()
+    yd, k2 = y._desc()
+    gp = (ctypes.c_void_p * y.d)(*[t.data_ptr() for t in g])
+    ws = _workspace(lib.tt_dot_grad_workspace(mode, ctypes.byref(xd), ctypes.byref(yd)),
+                    y.cores[0].device)
+    check(lib.tt_dot_grad(mode, ctypes.byref(xd), ctypes.byref(yd), gp,
+                          ctypes.c_void_p(ws.data_ptr()), ws.numel(), _stream(stream)))
+    return g
+
+
+def tt_local_dots(x: TT, y: TT, mats: Sequence[torch.Tensor], mode: int = MODE_FP64,
+                  stream=None) -> torch.Tensor:
+    """``out[k] = <x, (I x .. x mats[k] x .. x I) y>`` (float64 device tensor)."""
+    _check_dtype(x.cores + y.cores + list(mats), mode)
+    out = torch.empty(x.d, dtype=torch.float64, device=x.cores[0].device)
+    xd, k1 = x._desc()
+    yd, k2 = y._desc()
+    mp = (ctypes.c_void_p * x.d)(*[m.data_ptr() for m in mats])
+    ws = _workspace(lib.tt_local_dots_workspace(mode, ctypes.byref(xd), ctypes.byref(yd)),
+                    out.device)
+    check(lib.tt_local_dots(mode, ctypes.byref(xd), ctypes.byref(yd), mp,
+                            ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(ws.data_ptr()),
+                            ws.numel(), _stream(stream)))
+    return out
+
+
+def tt_kron_sum_op(mats: Sequence[torch.Tensor], theta=None, mode: int = MODE_FP64,
+                   stream=None) -> List[torch.Tensor]:
+    """Cores of ``sum_k theta_k (I x .. x mats[k] x .. x I)`` (rank 2)."""
+    _check_dtype(list(mats), mode)
+    d = len(mats)
+    ns = [m.shape[0] for m in mats]
+    R = [1] + [2] * (d - 1) + [1]
+    cores = [torch.empty((R[k], ns[k], ns[k], R[k + 1]), dtype=mats[0].dtype,
+                         device=mats[0].device) for k in range(d)]
+    n_arr = (ctypes.c_int64 * d)(*ns)
+    mp = (ctypes.c_void_p * d)(*[m.data_ptr() for m in mats])
+    cp = (ctypes.c_void_p * d)(*[c.data_ptr() for c in cores])
+    th = None
+    if theta is not None:
+        vals = [float(t) for t in (theta.detach().cpu().tolist() if torch.is_tensor(theta)
+                                   else theta)]
+        th = (ctypes.c_double * d)(*vals)
+    check(lib.tt_kron_sum_op(mode, d, n_arr, mp, th, cp, _stream(stream)))
+    return cores
+
+
+def tt_op_transpose(op: Sequence[torch.Tensor], mode: int = MODE_FP64,
+                    stream=None) -> List[torch.Tensor]:
+    """Cores of ``A^T``."""
+    _check_dtype(list(op), mode)
+    out = [torch.empty_like(c) for c in op]
+    od, k1 = _op_desc(op)
+    cp = (ctypes.c_void_p * len(op))(*[c.data_ptr() for c in out])
+    check(lib.tt_op_transpose(mode, ctypes.byref(od), cp, _stream(stream)))
+    return out
+
+
+class _SolveLoss(torch.autograd.Function):
+    """``loss(theta, b) = ||x - x_t||^2`` with ``A(theta) x = b`` and
+    ``A(theta) = sum_k theta_k (I x .. x M x .. x I)``.
+
+    Backward: ``lambda = A^{-T} 2 (x - x_t)`` by a second TT-sGMRES solve on the
+    transposed operator, then ``dL/dtheta_k = -<lambda, (I x .. M .. x I) x>``
+    (tt_local_dots), ``dL/db_k = d<lambda, b>/db_k`` and ``dL/dxt_k =
+    -d<2(x - x_t), x_t>/dxt_k`` (tt_dot_grad)."""
+
+    @staticmethod
+    def forward(ctx, theta, M, cfg, *cores):
+        d = cfg["d"]
+        b = TT(cores[:d])
+        xt = TT(cores[d:])
+        mats = [M] * d
+        op = tt_kron_sum_op(mats, theta)
+        x, info = tt_sgmres_solve(op, b, **cfg["solver"])
+        loss = (tt_dot(x, x) - 2.0 * tt_dot(x, xt) + tt_dot(xt, xt)).reshape(())
+        ctx.cfg = cfg
+        ctx.info = info
+        ctx.save_for_backward(theta, M, *x.cores, *cores)
+        ctx.xd = x.d
+        cfg["last_info"] = info
+        return loss
+
+    @staticmethod
+    def backward(ctx, gout):
+        cfg = ctx.cfg
+        d = cfg["d"]
+        saved = ctx.saved_tensors
+        theta, M = saved[0], saved[1]
+        x = TT(saved[2:2 + d])
+        b = TT(saved[2 + d:2 + 2 * d])
+        xt = TT(saved[2 + 2 * d:2 + 3 * d])
+        sv = cfg["solver"]
+        # right-hand side of the adjoint system: 2 (x - x_t), rounded in FP64
+        # far below the solver tolerance
+        rmax_r = max(x.ranks) + max(xt.ranks)
+        r = tt_round_rand([x, xt], [2.0, -2.0], 1e-12, rmax_r, oversample=sv.get("oversample", 10),
+                          seed=sv.get("seed", 0) + 1)
+        opT = tt_op_transpose(tt_kron_sum_op([M] * d, theta))
+        lam, info = tt_sgmres_solve(opT, r, **sv)
+        cfg["last_adjoint_info"] = info
+        g = gout.to(torch.float64)
+        dtheta = -tt_local_dots(lam, x, [M] * d) * g
+        db = [t * g for t in tt_dot_grad(lam, b)]
+        dxt = [-t * g for t in tt_dot_grad(r, xt)]
+        dtheta = dtheta.to(device=theta.device, dtype=theta.dtype)
+        return (dtheta, None, None, *db, *dxt)
+
+
+def solve_loss(theta: torch.Tensor, M: torch.Tensor, b_cores: Sequence[torch.Tensor],
+               xt_cores: Sequence[torch.Tensor], **solver) -> torch.Tensor:
+    """Differentiable ``||x(theta, b) - x_t||^2`` (float64 scalar on the device).
+
+    ``theta``: d coefficients; ``M``: the n x n 1-D operator (float64, CUDA);
+    ``b_cores``, ``xt_cores``: float64 CUDA cores.  ``solver``: keyword
+    arguments of :func:`tt_sgmres_solve` (``maxit``, ``tol``, ``rmax``,
+    ``mode``, ...), used for both the forward and the adjoint solve.  After a
+    call, ``solve_loss.last`` holds the forward and adjoint solver info."""
+    d = len(b_cores)
+    cfg = {"d": d, "solver": dict(solver)}
+    loss = _SolveLoss.apply(theta, M, cfg, *b_cores, *xt_cores)
+    solve_loss.last = cfg
+    return loss

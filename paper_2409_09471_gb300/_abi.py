@@ -81,6 +81,12 @@ def _load():
         "tt_sgmres_solve": (cint, [P(TTOp), P(TTVec), P(SolverParams), P(TTVecOut),
                                    P(SolverInfo), V, sz, V]),
         "tt_sgmres_solve_workspace": (sz, [P(TTOp), P(TTVec), P(SolverParams)]),
+        "tt_dot_grad": (cint, [cint, P(TTVec), P(TTVec), c_vpp, V, sz, V]),
+        "tt_dot_grad_workspace": (sz, [cint, P(TTVec), P(TTVec)]),
+        "tt_local_dots": (cint, [cint, P(TTVec), P(TTVec), c_vpp, V, V, sz, V]),
+        "tt_local_dots_workspace": (sz, [cint, P(TTVec), P(TTVec)]),
+        "tt_kron_sum_op": (cint, [cint, cint, c_i64p, c_vpp, P(dbl), c_vpp, V]),
+        "tt_op_transpose": (cint, [cint, P(TTOp), c_vpp, V]),
         "tt_profile": (cint, [cint]),
         "tt_profile_read": (cint, [cint, P(dbl), c_i64p, P(dbl), P(dbl)]),
         "tt_launch_count": (i64, []),

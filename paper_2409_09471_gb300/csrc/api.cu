@@ -381,6 +381,113 @@ int tt_gaussian(int mode, void* out, int64_t count, uint64_t seed, uint64_t stre
   });
 }
 
+namespace {
+template <typename T>
+void do_dot_grad(int mode, const tt_vec* x, const tt_vec* y, void* const* g, void* const* M,
+                 double* out, void* ws, size_t bytes, void* stream, bool dry) {
+  TTv<T> xv = view<T>(x, "x");
+  TTv<T> yv = view<T>(y, "y");
+  if (xv.d != yv.d) throw Error(TT_ERR_ARG, "dot_grad: d mismatch");
+  same_modes(xv.n, yv.n, xv.d, "dot_grad");
+  const int d = xv.d;
+  std::vector<T*> gp(d, nullptr);
+  std::vector<const T*> mp(d, nullptr);
+  if (!dry) {
+    if (M) {
+      if (!out) throw Error(TT_ERR_ARG, "local_dots: null out");
+      for (int k = 0; k < d; ++k)
+        if (!(mp[k] = (const T*)M[k])) throw Error(TT_ERR_ARG, "local_dots: null matrix");
+    }
+    if (g)
+      for (int k = 0; k < d; ++k)
+        if (!(gp[k] = (T*)g[k])) throw Error(TT_ERR_ARG, "dot_grad: null gradient core");
+  }
+  Carved cv = carve(mode, ws, bytes, stream, dry);
+  fix_ctx(cv);
+  tt_dot_grad_dev<T>(cv.ctx, xv, yv, g ? gp.data() : nullptr, M ? mp.data() : nullptr, out);
+  if (dry) throw (size_t)cv.ar.peak;
+}
+void* const kDryPtrs[1] = {nullptr};
+}  // namespace
+
+size_t tt_dot_grad_workspace(int mode, const tt_vec* x, const tt_vec* y) {
+  return measure([&] {
+    check_mode(mode);
+    if (mode == TT_MODE_FP64)
+      do_dot_grad<double>(mode, x, y, kDryPtrs, nullptr, nullptr, nullptr, 0, nullptr, true);
+    else
+      do_dot_grad<float>(mode, x, y, kDryPtrs, nullptr, nullptr, nullptr, 0, nullptr, true);
+  });
+}
+
+int tt_dot_grad(int mode, const tt_vec* x, const tt_vec* y, void* const* g, void* ws,
+                size_t ws_bytes, void* stream) {
+  return guarded([&] {
+    check_mode(mode);
+    if (!g) throw Error(TT_ERR_ARG, "dot_grad: null gradient array");
+    if (mode == TT_MODE_FP64)
+      do_dot_grad<double>(mode, x, y, g, nullptr, nullptr, ws, ws_bytes, stream, false);
+    else
+      do_dot_grad<float>(mode, x, y, g, nullptr, nullptr, ws, ws_bytes, stream, false);
+  });
+}
+
+size_t tt_local_dots_workspace(int mode, const tt_vec* x, const tt_vec* y) {
+  return measure([&] {
+    check_mode(mode);
+    if (mode == TT_MODE_FP64)
+      do_dot_grad<double>(mode, x, y, nullptr, kDryPtrs, nullptr, nullptr, 0, nullptr, true);
+    else
+      do_dot_grad<float>(mode, x, y, nullptr, kDryPtrs, nullptr, nullptr, 0, nullptr, true);
+  });
+}
+
+int tt_local_dots(int mode, const tt_vec* x, const tt_vec* y, void* const* M, double* out,
+                  void* ws, size_t ws_bytes, void* stream) {
+  return guarded([&] {
+    check_mode(mode);
+    if (!M) throw Error(TT_ERR_ARG, "local_dots: null matrix array");
+    if (mode == TT_MODE_FP64)
+      do_dot_grad<double>(mode, x, y, nullptr, M, out, ws, ws_bytes, stream, false);
+    else
+      do_dot_grad<float>(mode, x, y, nullptr, M, out, ws, ws_bytes, stream, false);
+  });
+}
+
+int tt_kron_sum_op(int mode, int d, const int64_t* n, void* const* M, const double* theta,
+                   void* const* cores, void* stream) {
+  return guarded([&] {
+    check_mode(mode);
+    if (d < 1 || d > MAXD || !n || !M || !cores) throw Error(TT_ERR_ARG, "kron_sum_op: bad arguments");
+    for (int k = 0; k < d; ++k)
+      if (n[k] < 1 || !M[k] || !cores[k]) throw Error(TT_ERR_ARG, "kron_sum_op: bad mode " + std::to_string(k));
+    if (mode == TT_MODE_FP64)
+      tt_kron_sum_op_dev<double>((cudaStream_t)stream, d, n, (const double* const*)M, theta,
+                                 (double* const*)cores);
+    else
+      tt_kron_sum_op_dev<float>((cudaStream_t)stream, d, n, (const float* const*)M, theta,
+                                (float* const*)cores);
+  });
+}
+
+int tt_op_transpose(int mode, const tt_op* A, void* const* cores, void* stream) {
+  return guarded([&] {
+    check_mode(mode);
+    if (!cores) throw Error(TT_ERR_ARG, "op_transpose: null output");
+    if (mode == TT_MODE_FP64) {
+      TTop<double> a = view_op<double>(A, 0);
+      for (int k = 0; k < a.d; ++k)
+        if (!cores[k]) throw Error(TT_ERR_ARG, "op_transpose: null output core");
+      tt_op_transpose_dev<double>((cudaStream_t)stream, a, (double* const*)cores);
+    } else {
+      TTop<float> a = view_op<float>(A, 0);
+      for (int k = 0; k < a.d; ++k)
+        if (!cores[k]) throw Error(TT_ERR_ARG, "op_transpose: null output core");
+      tt_op_transpose_dev<float>((cudaStream_t)stream, a, (float* const*)cores);
+    }
+  });
+}
+
 size_t tt_qr_f64_workspace(int64_t m, int64_t l) { return qr_workspace(m, l) + 64 * 1024; }
 
 int tt_qr_f64(int mode, const void* Y, int64_t m, int64_t l, int64_t sr, int64_t sc, void* Q,

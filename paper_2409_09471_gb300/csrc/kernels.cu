@@ -109,6 +109,25 @@ __global__ void sumsq_partial(const void* x, int f64, int64_t count, double* par
   }
 }
 
+__global__ void dot_partial(const void* a, const void* b, int f64, int64_t count, double* part) {
+  double acc = 0.0;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < count;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const double u = f64 ? ((const double*)a)[e] : (double)((const float*)a)[e];
+    const double v = f64 ? ((const double*)b)[e] : (double)((const float*)b)[e];
+    acc = fma(u, v, acc);
+  }
+  __shared__ double sh[32];
+  acc = warp_sum(acc);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double v = threadIdx.x < (blockDim.x >> 5) ? sh[threadIdx.x] : 0.0;
+    v = warp_sum(v);
+    if (threadIdx.x == 0) part[blockIdx.x] = v;
+  }
+}
+
 __global__ void sum_final(const double* part, int np, double* out) {
   double acc = 0.0;
   for (int i = threadIdx.x; i < np; i += blockDim.x) acc += part[i];
@@ -166,6 +185,16 @@ void sumsq(const void* x, int x_f64, int64_t count, double* out, double* scratch
   const int np = (int)std::min<int64_t>(std::max<int64_t>(ceil_div(count, 1024), 1), 256);
   sumsq_partial<<<np, 256, 0, st>>>(x, x_f64, count, scratch);
   check_launch("sumsq_partial");
+  sum_final<<<1, 256, 0, st>>>(scratch, np, out);
+  check_launch("sum_final");
+}
+
+void dot_acc(const void* a, const void* b, int f64, int64_t count, double* out, double* scratch,
+             cudaStream_t st) {
+  if (g_dry_run) return;
+  const int np = (int)std::min<int64_t>(std::max<int64_t>(ceil_div(count, 1024), 1), 256);
+  dot_partial<<<np, 256, 0, st>>>(a, b, f64, count, scratch);
+  check_launch("dot_partial");
   sum_final<<<1, 256, 0, st>>>(scratch, np, out);
   check_launch("sum_final");
 }

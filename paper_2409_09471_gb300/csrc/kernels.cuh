@@ -33,6 +33,9 @@ void gaussian_subblock(void* out, int out_f64, int64_t rows, int64_t n, int64_t 
 // out[0] = sum of squares of x[0..count) (FP64 accumulation); x float or double.
 void sumsq(const void* x, int x_f64, int64_t count, double* out, double* scratch,
            cudaStream_t st);
+// out[0] = sum_e a[e] b[e] (FP64 accumulation); a, b both float or both double.
+void dot_acc(const void* a, const void* b, int f64, int64_t count, double* out, double* scratch,
+             cudaStream_t st);
 // y[0] = sqrt(x[0]).
 void sqrt_scalar(const double* x, double* y, cudaStream_t st);
 

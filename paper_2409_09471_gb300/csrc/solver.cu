@@ -112,7 +112,11 @@ SolveResult sgmres_solve(const Ctx& c0, const TTop<double>& A64in, const TTv<dou
   DRMSource<T> drm;
   drm.seed = p.seed;
   drm.L[0] = drm.L[d] = 1;
-  for (int k = 1; k < d; ++k) drm.L[k] = std::max(p.rmax, r_sol) + p.oversample;
+  // capacity: every rounding's rank cap (basis rmax, solution r_sol, and the
+  // right-hand side's own ranks, which cap the restart residual) plus p
+  int64_t rb_drm = 1;
+  for (int k = 0; k <= d; ++k) rb_drm = std::max(rb_drm, b.r[k]);
+  for (int k = 1; k < d; ++k) drm.L[k] = std::max(std::max(p.rmax, r_sol), rb_drm) + p.oversample;
   std::vector<T*> drm_cores(d);
   std::vector<double*> drm64_cores(d);
   for (int k = 0; k < d; ++k) {

@@ -42,6 +42,19 @@ void tt_sketch_dev(const Ctx& c, const TTv<T>& x, int64_t s, const T* const* S, 
 
 template <typename T>
 void tt_dot_dev(const Ctx& c, const TTv<T>& x, const TTv<T>& y, double* out);
+// Derivative of <x, y> with respect to every core of y (g[k] shaped like
+// y's core k; nullptr skips it) and, when M is given, dots[k] = <x, (I x .. x
+// M[k] x .. x I) y> in FP64 (adjoint.cu).
+template <typename T>
+void tt_dot_grad_dev(const Ctx& c, const TTv<T>& x, const TTv<T>& y, T* const* g,
+                     const T* const* M, double* dots);
+// Cores of the rank-2 operator sum_k theta_k (I x .. x M[k] x .. x I).
+template <typename T>
+void tt_kron_sum_op_dev(cudaStream_t st, int d, const int64_t* n, const T* const* M,
+                        const double* theta, T* const* cores);
+// Cores of A^T (input and output mode indices swapped in every core).
+template <typename T>
+void tt_op_transpose_dev(cudaStream_t st, const TTop<T>& A, T* const* cores);
 
 // Randomize-then-orthogonalize rounding of sum_b terms[b] into y (cores with
 // capacity; y.r[] is filled in).  Returns after a stream synchronisation.

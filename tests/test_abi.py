@@ -60,3 +60,27 @@ def test_argument_errors_are_caught_on_the_host(built_lib):
     assert rc == 1 and b"null descriptor" in lib.tt_last_error()
     rc = lib.tt_matvec(7, None, None, None, None, 0, None)
     assert rc == 1 and b"unknown mode" in lib.tt_last_error()
+
+
+def test_workspace_queries_run_without_a_gpu(built_lib):
+    # every *_workspace entry point is a dry run on the host (no CUDA call):
+    # descriptors with placeholder device pointers must give a positive size
+    from paper_2409_09471_gb300 import _abi
+    lib = _abi.lib
+    d, ns = 4, [7, 5, 8, 6]
+
+    def desc(ranks):
+        n = (ctypes.c_int64 * d)(*ns)
+        r = (ctypes.c_int64 * (d + 1))(*ranks)
+        p = (ctypes.c_void_p * d)(*([0x1000] * d))
+        return _abi.TTVec(d, n, r, p), (n, r, p)
+
+    x, kx = desc([1, 4, 9, 3, 1])
+    y, ky = desc([1, 2, 6, 5, 1])
+    for mode in (0, 1, 2):
+        assert lib.tt_dot_workspace(mode, ctypes.byref(x), ctypes.byref(y)) > 0
+        assert lib.tt_dot_grad_workspace(mode, ctypes.byref(x), ctypes.byref(y)) > 0
+        assert lib.tt_local_dots_workspace(mode, ctypes.byref(x), ctypes.byref(y)) > 0
+        assert lib.tt_sketch_workspace(mode, ctypes.byref(x), 40) > 0
+        arr = (_abi.TTVec * 2)(x, y)
+        assert lib.tt_round_rand_workspace(mode, 2, arr, 8, 4) > 0

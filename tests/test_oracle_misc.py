@@ -91,3 +91,47 @@ def test_dense_adjoint_vs_finite_differences():
             fd = (adjoint.loss_and_grads(theta, L, bp, xt)[0]
                   - adjoint.loss_and_grads(theta, L, bm, xt)[0]) / (2 * h)
             assert np.isclose(dcores[k][idx], fd, rtol=1e-5, atol=1e-9)
+
+
+def test_tt_dot_grad_matches_dense_and_fd():
+    # the TT restatement against the dense gradient of <X, Y> (interfaces of y
+    # built from full tensors) and against central differences
+    ns = [3, 4, 2, 3]
+    x = ti.random_tt(ns, [1, 2, 3, 2, 1], seed=11)
+    y = ti.random_tt(ns, [1, 3, 2, 2, 1], seed=12)
+    G = adjoint.dot_grad(x, y)
+    X = tt.full(x)
+    for k in range(len(ns)):
+        left = np.ones((1, 1))
+        for c in y[:k]:
+            left = (left @ c.reshape(c.shape[0], -1)).reshape(-1, c.shape[2])
+        right = np.ones((1, 1))
+        for c in reversed(y[k + 1:]):
+            right = (c.reshape(-1, c.shape[2]) @ right.T).reshape(c.shape[0], -1).T
+        Xk = X.reshape(left.shape[0], ns[k], right.shape[0])
+        dense = np.einsum("xiy,xa,yc->aic", Xk, left, right)
+        assert np.allclose(G[k], dense, atol=1e-12)
+    h = 1e-6
+    for k, idx in [(0, (0, 1, 2)), (2, (1, 0, 1)), (3, (1, 2, 0))]:
+        yp = [c.copy() for c in y]
+        ym = [c.copy() for c in y]
+        yp[k][idx] += h
+        ym[k][idx] -= h
+        fd = (tt.dot(x, yp) - tt.dot(x, ym)) / (2 * h)
+        assert np.isclose(G[k][idx], fd, rtol=1e-7, atol=1e-10)
+
+
+def test_tt_local_dots_match_dense_mode_products():
+    ns = [4, 3, 5]
+    x = ti.random_tt(ns, [1, 2, 3, 1], seed=13)
+    y = ti.random_tt(ns, [1, 3, 2, 1], seed=14)
+    rng = np.random.default_rng(15)
+    mats = [rng.standard_normal((n, n)) for n in ns]
+    out = adjoint.local_dots(x, y, mats)
+    X, Y = tt.full(x).reshape(ns), tt.full(y).reshape(ns)
+    for k in range(3):
+        MY = np.moveaxis(np.tensordot(mats[k], Y, axes=([1], [k])), 0, k)
+        assert np.isclose(out[k], np.sum(X * MY), rtol=1e-12)
+    # a Kronecker-sum term with M = identity gives <x, y> in every position
+    ones = adjoint.local_dots(x, y, [np.eye(n) for n in ns])
+    assert np.allclose(ones, tt.dot(x, y), rtol=1e-12)

@@ -198,6 +198,9 @@ def workload(name: str, **over) -> Workload:
       rmax 40, m<=100, s=200.
     * ``differentiable``  d=12, n=64, ``A(theta) = sum_k theta_k L_k`` with
       ``theta_k ~ U[0.5, 2]``, b and x_target random TT rank 4, rmax 64.
+      x_target is scaled by ``1 / lambda_min(A(theta))`` (the largest gain of
+      ``A^{-1}`` on a unit right-hand side), so that it has the solution's
+      order of magnitude and the loss is sensitive to theta.
     """
     if name == "laplace_fp64":
         d, n = over.get("d", 4), over.get("n", 16)
@@ -242,6 +245,8 @@ def workload(name: str, **over) -> Workload:
         L = laplacian_1d(n)
         b = random_tt([n] * d, [1] + [4] * (d - 1) + [1], seed=over.get("seed", 2))
         xt = random_tt([n] * d, [1] + [4] * (d - 1) + [1], seed=over.get("target_seed", 3))
+        lam_min = float(np.sum(theta)) * 4.0 * (n + 1) ** 2 * np.sin(np.pi / (2 * (n + 1))) ** 2
+        xt[0] = xt[0] / lam_min
         op = kron_sum_operator([t * L for t in theta])
         maxit = over.get("maxit", 100)
         params = dict(maxit=maxit, s=2 * maxit, tol=1e-6, rmax=64, oversample=10, mode="fp32",
