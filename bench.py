@@ -62,9 +62,14 @@ def parse():
     ap.add_argument("--no-fp64-leg", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=20.0,
                     help="budget of the host oracle sample")
-    ap.add_argument("--case", choices=["solve", "round"], default="solve",
+    ap.add_argument("--case", choices=["solve", "round", "batched"], default="solve",
                     help="'round': time one randomized rounding of w - h v at the workload's "
-                         "sizes (the kernel-level case used for ncu captures)")
+                         "sizes (the kernel-level case used for ncu captures); 'batched': the "
+                         "64-right-hand-side workload through the batched solver")
+    ap.add_argument("--workers", type=int, default=16,
+                    help="library worker threads (streams) of the batched case")
+    ap.add_argument("--seq-sample", type=int, default=4,
+                    help="right-hand sides timed one at a time for the batched case's baseline")
     return ap.parse_args()
 
 
@@ -420,10 +425,62 @@ def run_round_case(args):
                       "out_ranks": y.ranks}), flush=True)
 
 
+def run_batched_case(args):
+    """The batched workload: 64 right-hand sides (d=8, n=32 Laplacian, bond
+    ranks U{1..12}, rank cap 150), solved by the library's worker pool in the
+    selected mode; one JSON line with the whole-batch time and RHS/s."""
+    import torch
+    import paper_2409_09471_gb300 as g
+    mode_name = args.mode or "tf32"
+    mode = {"tf32": g.MODE_TF32, "fp32": g.MODE_FP32, "fp64": g.MODE_FP64}[mode_name]
+    w = ti.workload("batched")
+    p = w.params
+    op = g.op_to_device(w.op)
+    bs = [g.TT.from_numpy(b) for b in w.b]
+    kw = dict(maxit=p["maxit"], tol=p["tol"], rmax=p["rmax"], mode=mode, s=p["s"],
+              round_tol=p["round_tol"], r_sol=p["r_sol"], oversample=p["oversample"],
+              max_restarts=10, nworkers=args.workers)
+    times = []
+    for i in range(args.warmup + args.steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        res = g.tt_sgmres_solve_batched(op, bs, **kw)
+        torch.cuda.synchronize()
+        if i >= args.warmup:
+            times.append(time.perf_counter() - t0)
+    st = [r[1]["status"] for r in res]
+    tr = [r[1]["true_res"] for r in res]
+    it = [r[1]["iters"] for r in res]
+    sec = statistics.median(times)
+    # the same right-hand sides one at a time through the single-RHS solver
+    # (a bounded sample, projected to the batch by the batch's iteration counts)
+    seq_kw = {k: v for k, v in kw.items() if k != "nworkers"}
+    seq_t, seq_it = 0.0, 0
+    for b in bs[:args.seq_sample]:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, inf = g.tt_sgmres_solve(op, b, **seq_kw)
+        torch.cuda.synchronize()
+        seq_t += time.perf_counter() - t0
+        seq_it += inf["iters"]
+    line = {"case": "batched", "mode": mode_name, "nrhs": len(bs), "workers": args.workers,
+            "seconds": sec, "rhs_per_s": len(bs) / sec,
+            "not_converged": int(sum(s != 0 for s in st)), "max_true_res": max(tr),
+            "iters_mean": float(np.mean(it)), "iters_max": int(max(it))}
+    if seq_it:
+        proj = seq_t / seq_it * float(np.sum(it))
+        line["sequential"] = {"sample_rhs": args.seq_sample, "sample_seconds": seq_t,
+                              "projected_seconds": proj, "batched_speedup": proj / sec}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.case == "round":
         run_round_case(args)
+        return
+    if args.case == "batched":
+        run_batched_case(args)
         return
     if args.impl == "reference":
         run_reference(args)

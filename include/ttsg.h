@@ -243,6 +243,18 @@ int tt_qr_f64(int mode, const void* Y, int64_t m, int64_t l, int64_t sr, int64_t
 size_t tt_qr_f64_workspace(int64_t m, int64_t l);
 
 /*
+ * tt_qr_f64_batched - FP64 Householder QR of count independent tall matrices
+ * in one launch, one CTA per matrix with its rows in global memory (the form
+ * batched solves use; Sec. 3.3's QR).  Y[i] (device): m[i] x l[i] row-major in
+ * the mode's precision; Q[i] (device, may be NULL): m[i] x l[i] row-major, same
+ * precision; R[i] (device double, may be NULL): l[i] x l[i] upper triangular.
+ * m, l: host arrays.  Requires m[i] >= l[i] >= 1.
+ */
+int tt_qr_f64_batched(int mode, int count, void* const* Y, const int64_t* m, const int64_t* l,
+                      void* const* Q, double* const* R, void* ws, size_t ws_bytes, void* stream);
+size_t tt_qr_f64_batched_workspace(int count, const int64_t* m, const int64_t* l);
+
+/*
  * tt_lstsq_f64 - sketched least squares of eq. pseudo_inv:
  *   y = argmin ||W y - c||_2 with W (s x k, column-major, device double) and
  * c (device double[s]); writes y (device double[k]) and res = ||W y - c||
@@ -295,6 +307,24 @@ int tt_sgmres_solve(const tt_op* A, const tt_vec* b, const tt_solver_params* p,
                     const tt_vec_out* x, tt_solver_info* info, void* ws, size_t ws_bytes,
                     void* stream);
 size_t tt_sgmres_solve_workspace(const tt_op* A, const tt_vec* b, const tt_solver_params* p);
+
+/*
+ * tt_sgmres_solve_batched - nrhs independent solves A x_i = b_i (same operator,
+ * same parameters, uneven TT ranks allowed), each exactly as tt_sgmres_solve.
+ * The library runs them on min(nworkers, nrhs) worker threads of its own, each
+ * with its own CUDA stream and workspace slice; inside a batch every Householder
+ * QR runs on the fewest CTAs whose row blocks fit in shared memory, so the
+ * factorisations of different right-hand sides run side by side on different
+ * SMs.
+ * b, x, info: host arrays of nrhs descriptors (info may be NULL).  Returns
+ * TT_ERR_NOT_CONVERGED if any right-hand side stopped above tol (its info says
+ * which), another TT_ERR_* if a solve failed.  Synchronises.
+ */
+int tt_sgmres_solve_batched(const tt_op* A, int nrhs, const tt_vec* b, const tt_solver_params* p,
+                            const tt_vec_out* x, tt_solver_info* info, int nworkers, void* ws,
+                            size_t ws_bytes);
+size_t tt_sgmres_solve_batched_workspace(const tt_op* A, int nrhs, const tt_vec* b,
+                                         const tt_solver_params* p, int nworkers);
 
 /*
  * Measurement support (no counterpart in the method): tt_profile(mask) clears

@@ -29,7 +29,8 @@ from ._abi import (lib, TTVec, TTVecOut, TTOp, SolverParams, SolverInfo, MODE_FP
 __all__ = ["TT", "tt_matvec", "tt_sketch", "tt_dot", "tt_round_rand", "tt_gaussian", "tt_qr_f64",
            "tt_lstsq_f64", "tt_sgmres_solve", "MODE_FP64", "MODE_FP32", "MODE_TF32", "TTError",
            "LIB_PATH", "mode_dtype", "op_to_device", "tt_dot_grad", "tt_local_dots",
-           "tt_kron_sum_op", "tt_op_transpose", "solve_loss"]
+           "tt_kron_sum_op", "tt_op_transpose", "solve_loss", "tt_qr_f64_batched",
+           "tt_sgmres_solve_batched"]
 
 
 def mode_dtype(mode: int) -> torch.dtype:
@@ -407,3 +408,86 @@ def solve_loss(theta: torch.Tensor, M: torch.Tensor, b_cores: Sequence[torch.Ten
     loss = _SolveLoss.apply(theta, M, cfg, *b_cores, *xt_cores)
     solve_loss.last = cfg
     return loss
+
+
+# ------------------------------------------------------------------ batched
+def tt_qr_f64_batched(Ys: Sequence[torch.Tensor], want_q: bool = True, stream=None):
+    """FP64 Householder QR of several tall matrices in one launch (one CTA per
+    matrix); returns lists ``Q`` (each in its Y's dtype) and ``R`` (float64)."""
+    mode = MODE_FP64 if Ys[0].dtype == torch.float64 else MODE_FP32
+    _check_dtype(list(Ys), mode)
+    cnt = len(Ys)
+    ms = [y.shape[0] for y in Ys]
+    ls = [y.shape[1] for y in Ys]
+    Qs = [torch.empty_like(y) for y in Ys] if want_q else None
+    Rs = [torch.zeros((l, l), dtype=torch.float64, device=y.device) for y, l in zip(Ys, ls)]
+    m_arr = (ctypes.c_int64 * cnt)(*ms)
+    l_arr = (ctypes.c_int64 * cnt)(*ls)
+    yp = (ctypes.c_void_p * cnt)(*[y.data_ptr() for y in Ys])
+    qp = (ctypes.c_void_p * cnt)(*[q.data_ptr() for q in Qs]) if want_q else None
+    rp = (ctypes.c_void_p * cnt)(*[r.data_ptr() for r in Rs])
+    ws = _workspace(lib.tt_qr_f64_batched_workspace(cnt, m_arr, l_arr), Ys[0].device)
+    check(lib.tt_qr_f64_batched(mode, cnt, yp, m_arr, l_arr, qp, rp, ctypes.c_void_p(ws.data_ptr()),
+                                ws.numel(), _stream(stream)))
+    return Qs, Rs
+
+
+def tt_sgmres_solve_batched(op, bs: Sequence[TT], maxit: int, tol: float, rmax: int,
+                            mode: int = MODE_FP64, s: int = 0, round_tol: float = 0.0,
+                            eta: float = 0.1, stop_safety: float = 0.1, r_sol: int = 0,
+                            oversample: int = 10, seed: int = 0, max_restarts: int = 5,
+                            nworkers: int = 16, workspace=None):
+    """Independent solves ``A x_i = b_i`` for all right-hand sides (uneven ranks
+    allowed) on ``nworkers`` library threads and streams.  Returns a list of
+    ``(x_i, info_i)`` like :func:`tt_sgmres_solve`; synchronises."""
+    _check_dtype(list(op) + [c for b in bs for c in b.cores], MODE_FP64)
+    p = SolverParams(maxit, s, tol, round_tol, eta, stop_safety, rmax, r_sol, oversample, seed,
+                     max_restarts, mode)
+    nrhs = len(bs)
+    od, k1 = _op_desc(op)
+    descs, keep = [], []
+    for b in bs:
+        dsc, k = b._desc()
+        descs.append(dsc)
+        keep.append(k)
+    barr = (TTVec * nrhs)(*descs)
+    dev = bs[0].cores[0].device
+    need = lib.tt_sgmres_solve_batched_workspace(ctypes.byref(od), nrhs, barr, ctypes.byref(p),
+                                                 nworkers)
+    if need == 0:
+        raise TTError(1, lib.tt_last_error().decode())
+    if workspace is None or workspace.numel() < need:
+        workspace = _workspace(need, dev)
+    rs = r_sol if r_sol > 0 else rmax
+    outs, odescs = [], []
+    infos = (SolverInfo * nrhs)()
+    for i, b in enumerate(bs):
+        d = b.d
+        cap = [1] + [rs] * (d - 1) + [1]
+        xc = [torch.empty(cap[k] * b.ns[k] * cap[k + 1], dtype=torch.float64, device=dev)
+              for k in range(d)]
+        n_arr = (ctypes.c_int64 * d)(*b.ns)
+        cap_arr = (ctypes.c_int64 * (d + 1))(*cap)
+        rank_arr = (ctypes.c_int64 * (d + 1))()
+        xp = (ctypes.c_void_p * d)(*[c.data_ptr() for c in xc])
+        odescs.append(TTVecOut(d, n_arr, cap_arr, rank_arr, xp))
+        outs.append((xc, rank_arr, n_arr, cap_arr, xp))
+        infos[i].hist_cap = 0
+    xarr = (TTVecOut * nrhs)(*odescs)
+    torch.cuda.synchronize(dev)
+    rc = lib.tt_sgmres_solve_batched(ctypes.byref(od), nrhs, barr, ctypes.byref(p), xarr, infos,
+                                     int(nworkers), ctypes.c_void_p(workspace.data_ptr()),
+                                     workspace.numel())
+    if rc not in (0, 5):
+        check(rc)
+    res = []
+    for i, b in enumerate(bs):
+        xc = outs[i][0]
+        r = list(xarr[i].rank[k] for k in range(b.d + 1))
+        x = TT([xc[k][: r[k] * b.ns[k] * r[k + 1]].view(r[k], b.ns[k], r[k + 1]) for k in range(b.d)])
+        inf = infos[i]
+        res.append((x, dict(iters=inf.iters, cycles=inf.cycles, sketched_res=inf.sketched_res,
+                            true_res=inf.true_res, max_rank=inf.max_rank, status=inf.status,
+                            seconds=inf.seconds, svd_nonconverged=inf.svd_nonconverged,
+                            workspace_bytes=int(need))))
+    return res

@@ -81,6 +81,11 @@ def _load():
         "tt_sgmres_solve": (cint, [P(TTOp), P(TTVec), P(SolverParams), P(TTVecOut),
                                    P(SolverInfo), V, sz, V]),
         "tt_sgmres_solve_workspace": (sz, [P(TTOp), P(TTVec), P(SolverParams)]),
+        "tt_sgmres_solve_batched": (cint, [P(TTOp), cint, P(TTVec), P(SolverParams), P(TTVecOut),
+                                           P(SolverInfo), cint, V, sz]),
+        "tt_sgmres_solve_batched_workspace": (sz, [P(TTOp), cint, P(TTVec), P(SolverParams), cint]),
+        "tt_qr_f64_batched": (cint, [cint, cint, c_vpp, c_i64p, c_i64p, c_vpp, c_vpp, V, sz, V]),
+        "tt_qr_f64_batched_workspace": (sz, [cint, c_i64p, c_i64p]),
         "tt_dot_grad": (cint, [cint, P(TTVec), P(TTVec), c_vpp, V, sz, V]),
         "tt_dot_grad_workspace": (sz, [cint, P(TTVec), P(TTVec)]),
         "tt_local_dots": (cint, [cint, P(TTVec), P(TTVec), c_vpp, V, V, sz, V]),

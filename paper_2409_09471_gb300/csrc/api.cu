@@ -3,6 +3,8 @@
 // and translation of exceptions into status codes.
 #include "solver.cuh"
 #include <chrono>
+#include <mutex>
+#include <thread>
 #include <cmath>
 
 namespace ttsg {
@@ -588,5 +590,123 @@ int tt_sgmres_solve(const tt_op* A, const tt_vec* b, const tt_solver_params* p,
                     const tt_vec_out* x, tt_solver_info* info, void* ws, size_t ws_bytes,
                     void* stream) {
   return guarded([&] { do_solve(A, b, p, x, info, ws, ws_bytes, stream, false); });
+}
+
+// ------------------------------------------------------------ batched forms
+namespace {
+struct NarrowQR {
+  bool old;
+  NarrowQR() : old(g_qr_narrow) { g_qr_narrow = true; }
+  ~NarrowQR() { g_qr_narrow = old; }
+};
+size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
+
+// Workspace of one solve whose QRs take the narrow form.
+size_t solve_bytes_narrow(const tt_op* A, const tt_vec* b, const tt_solver_params* p) {
+  NarrowQR f;
+  return measure([&] { do_solve(A, b, p, nullptr, nullptr, nullptr, 0, nullptr, true); });
+}
+
+size_t batched_slice(const tt_op* A, int nrhs, const tt_vec* b, const tt_solver_params* p) {
+  size_t mx = 0;
+  for (int i = 0; i < nrhs; ++i) {
+    const size_t s = solve_bytes_narrow(A, &b[i], p);
+    if (s == 0) throw Error(TT_ERR_ARG, "rhs " + std::to_string(i) + ": " + g_last_error);
+    mx = std::max(mx, s);
+  }
+  return align256(mx);
+}
+}  // namespace
+
+size_t tt_qr_f64_batched_workspace(int count, const int64_t* m, const int64_t* l) {
+  if (count < 1 || !m || !l) return 0;
+  return qr_batch_workspace(count, m, l) + 64 * 1024;
+}
+
+int tt_qr_f64_batched(int mode, int count, void* const* Y, const int64_t* m, const int64_t* l,
+                      void* const* Q, double* const* R, void* ws, size_t ws_bytes, void* stream) {
+  return guarded([&] {
+    check_mode(mode);
+    if (count < 1 || !Y || !m || !l) throw Error(TT_ERR_ARG, "qr_batched: bad arguments");
+    std::vector<QRProblem> pb(count);
+    const int f64 = mode == TT_MODE_FP64;
+    for (int i = 0; i < count; ++i) {
+      if (!Y[i] || m[i] < l[i] || l[i] < 1)
+        throw Error(TT_ERR_ARG, "qr_batched: problem " + std::to_string(i) + " needs Y and m >= l >= 1");
+      pb[i] = QRProblem{Y[i], f64, m[i], l[i], l[i], 1, Q ? Q[i] : nullptr, f64, l[i],
+                        R ? R[i] : nullptr};
+    }
+    Carved cv = carve(mode, ws, ws_bytes, stream, false, false);
+    fix_ctx(cv);
+    reset_flags(cv);
+    const size_t need = qr_batch_workspace(count, m, l);
+    void* qw = cv.ar.take<char>((int64_t)need);
+    qr_f64_batched(count, pb.data(), qw, need, cv.ctx.err, cv.ctx.st);
+    check_device_flags(cv.ctx);
+  });
+}
+
+size_t tt_sgmres_solve_batched_workspace(const tt_op* A, int nrhs, const tt_vec* b,
+                                         const tt_solver_params* p, int nworkers) {
+  try {
+    if (nrhs < 1 || !b) throw Error(TT_ERR_ARG, "solve_batched: nrhs >= 1 and b required");
+    const int W = std::max(1, std::min(nworkers, nrhs));
+    return (size_t)W * batched_slice(A, nrhs, b, p);
+  } catch (const Error& e) {
+    g_last_error = e.what();
+    return 0;
+  }
+}
+
+int tt_sgmres_solve_batched(const tt_op* A, int nrhs, const tt_vec* b, const tt_solver_params* p,
+                            const tt_vec_out* x, tt_solver_info* info, int nworkers, void* ws,
+                            size_t ws_bytes) {
+  return guarded([&] {
+    if (nrhs < 1 || !b || !x) throw Error(TT_ERR_ARG, "solve_batched: nrhs >= 1, b and x required");
+    if (!ws) throw Error(TT_ERR_WORKSPACE, "null workspace");
+    const int W = std::max(1, std::min(nworkers, nrhs));
+    const size_t per = batched_slice(A, nrhs, b, p);
+    if (ws_bytes < (size_t)W * per)
+      throw Error(TT_ERR_WORKSPACE, "solve_batched: workspace below " + std::to_string(W * per));
+    int dev = 0;
+    TT_CUDA(cudaGetDevice(&dev));
+    std::mutex mu;
+    int first_err = 0, not_conv = 0;
+    std::string msg;
+    std::vector<std::thread> pool;
+    for (int w = 0; w < W; ++w) {
+      pool.emplace_back([&, w] {
+        cudaSetDevice(dev);
+        g_qr_narrow = true;
+        cudaStream_t st = nullptr;
+        if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
+          std::lock_guard<std::mutex> lk(mu);
+          if (!first_err) { first_err = TT_ERR_CUDA; msg = "solve_batched: stream creation failed"; }
+          return;
+        }
+        char* slice = (char*)ws + (size_t)w * per;
+        for (int i = w; i < nrhs; i += W) {
+          const int rc = guarded([&] {
+            do_solve(A, &b[i], p, &x[i], info ? &info[i] : nullptr, slice, per, st, false);
+          });
+          if (rc == TT_ERR_NOT_CONVERGED) {
+            std::lock_guard<std::mutex> lk(mu);
+            ++not_conv;
+          } else if (rc != TT_OK) {
+            if (info) info[i].status = rc;
+            std::lock_guard<std::mutex> lk(mu);
+            if (!first_err) { first_err = rc; msg = "rhs " + std::to_string(i) + ": " + g_last_error; }
+          }
+        }
+        cudaStreamSynchronize(st);
+        cudaStreamDestroy(st);
+      });
+    }
+    for (auto& t : pool) t.join();
+    if (first_err) throw Error(first_err, msg);
+    if (not_conv)
+      throw Error(TT_ERR_NOT_CONVERGED, std::to_string(not_conv) + " of " + std::to_string(nrhs) +
+                                            " right-hand sides stopped above tol");
+  });
 }
 

@@ -44,6 +44,24 @@ void sqrt_scalar(const double* x, double* y, cudaStream_t st);
 // double) on a cooperative grid.  Writes Q (m x l, row-major, ldq, float or
 // double) when Q != nullptr and R (l x l row-major double) when R != nullptr.
 size_t qr_workspace(int64_t m, int64_t l);
+// One matrix of a batched QR (Y element (i,j) at Y[i*sr + j*sc]).
+struct QRProblem {
+  const void* Y;
+  int y_f64;
+  int64_t m, l, sr, sc;
+  void* Q;
+  int q_f64;
+  int64_t ldq;
+  double* R;
+};
+// Batched form: one CTA per matrix, rows in global memory, one launch.
+size_t qr_batch_workspace(int count, const int64_t* m, const int64_t* l);
+void qr_f64_batched(int count, const QRProblem* probs, void* ws, size_t ws_bytes, int* err_flag,
+                    cudaStream_t st);
+// When set on the calling thread, qr_f64 uses the narrow cooperative form: the
+// fewest CTAs whose row blocks fit in shared memory (many independent solves
+// running side by side on their own streams).
+extern thread_local bool g_qr_narrow;
 void qr_f64(const void* Y, int y_f64, int64_t m, int64_t l, int64_t sr, int64_t sc, void* Q,
             int q_f64, int64_t ldq, double* R, void* ws, size_t ws_bytes, int* err_flag,
             cudaStream_t st);
@@ -74,7 +92,7 @@ void chol_f64_batched(int count, const double* const* G, const int64_t* l, doubl
 // A sweep cap reached without convergence increments *err_flag.
 void jacobi_svd(const double* G, int64_t l, int trans, int f32, double* GV, double* V, double* sigma,
                 double eps, int64_t dm1, int64_t rmax, const double* norm_in, double* norm_out,
-                int* rank_out, int* err_flag, cudaStream_t st);
+                int* rank_out, int* err_flag, cudaStream_t st, double* vtmp = nullptr);
 
 // Batched form: one CTA per problem; every problem uses the same rank rule
 // parameters.  With norm_in == nullptr each problem takes its own sqrt(sum
@@ -92,6 +110,7 @@ struct JacobiBatchArgs {
   double* V[TT_MAX_D] = {};
   double* sigma[TT_MAX_D] = {};
   int* rank_out[TT_MAX_D] = {};
+  double* vtmp[TT_MAX_D] = {};  // l x l scratch each, used when l is too large for shared memory
 };
 void jacobi_svd_batched(const JacobiBatchArgs& a, cudaStream_t st);
 

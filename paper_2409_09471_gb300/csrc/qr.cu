@@ -64,6 +64,9 @@ struct QRArgs {
   int ldy;         // shared-memory row stride (l + 1)
   int nown;        // rows of T per CTA
   int cw;          // Q-formation column chunk
+  double* Yg;      // one-CTA mode: working copy of Y in global memory (else null)
+  float* Vfg;      // one-CTA mode: float reflectors [m][l]
+  float* yjfg;     // one-CTA mode: float column j [m]
 };
 
 __device__ __forceinline__ double warp_sum(double v) {
@@ -140,28 +143,51 @@ __device__ void form_q(const QRArgs& a, const E* Vr, int ldv, E* Kc, int nloc, i
   }
 }
 
-__global__ void __launch_bounds__(QR_THREADS) qr_coop_kernel(const QRArgs a) {
+// Grid-wide synchronisation of one factorisation: the block barrier when one
+// CTA owns the whole matrix, otherwise the bounded grid barrier.
+__device__ __forceinline__ bool sync_all(const QRArgs& a, int P, unsigned& target) {
+  if (P == 1) {
+    __syncthreads();
+    return true;
+  }
+  return grid_barrier(a.bar, target, a.err);
+}
+
+// The factorisation of one matrix by P CTAs (CTA c of P).  gm: the rows and the
+// float copies live in global memory (one CTA per matrix, batched launches);
+// otherwise CTA c keeps its row block in shared memory.
+__device__ __forceinline__ void qr_body(const QRArgs& a, int P, int c, bool gm) {
   extern __shared__ double smem[];
   const int l = (int)a.l, ldy = a.ldy;
-  const int P = gridDim.x, c = blockIdx.x, tid = threadIdx.x;
+  const int tid = threadIdx.x;
   const int warp = tid >> 5, lane = tid & 31;
   const bool want_q = a.Q != nullptr;
   // float Q: the compact-WY products (columns < j) run on the FP32 pipe from a
   // float copy of the normalised reflectors (also the V operand of form_q)
   const bool tf = want_q && !a.q_f64;
-  double* Yl = smem;                                     // [rows][ldy]: R above, v below
-  double* ts = Yl + (size_t)a.rows * ldy;                // [l] reduced sums t_c
+  double* sp = smem;
+  double* Yl = gm ? a.Yg : sp;                           // [rows][ldy]: R above, v below
+  if (!gm) sp += (size_t)a.rows * ldy;
+  double* ts = sp;                                       // [l] reduced sums t_c
   double* rj = ts + l;                                   // [l] published row j
   double* uu = rj + l;                                   // [l] u_c (tau u_c for c > j)
   double* part = uu + l;                                 // [QR_RPMAX][l]
   double* Tl = part + (size_t)QR_RPMAX * l;              // [nown][l] owned rows of T
   float* partf = (float*)(Tl + (size_t)a.nown * l);      // [QR_RPMAX][l]
-  float* yjf = partf + (size_t)QR_RPMAX * l;             // [rows] column j in float
-  float* Vf = yjf + a.rows;                              // [rows][l] reflectors in float
+  float* fp = partf + (size_t)QR_RPMAX * l;
+  float* yjf = gm ? a.yjfg : fp;                         // [rows] column j in float
+  if (!gm) fp += a.rows;
+  float* Vf = gm ? a.Vfg : fp;                           // [rows][l] reflectors in float
+  if (!gm && tf) fp += (size_t)a.rows * l;
   unsigned char* qx =                                    // Q-formation chunk, 16-byte aligned
-      (unsigned char*)(((uintptr_t)(Vf + (tf ? (size_t)a.rows * l : 0)) + 15) & ~(uintptr_t)15);
+      (unsigned char*)(((uintptr_t)fp + 15) & ~(uintptr_t)15);
   __shared__ double hs[4];  // beta, tau, scale of the current reflector
   unsigned btarget = 0;  // running grid-barrier target (used by thread 0)
+  if (gm) {
+    // one CTA: its own reduction slots are cleared here instead of by the host
+    for (int e = tid; e < NREP * l * l; e += QR_THREADS) a.acc[e] = 0.0;
+    __syncthreads();
+  }
   const int64_t r0 = (int64_t)c * a.rows;
   const int64_t r1 = a.m < r0 + a.rows ? a.m : r0 + a.rows;
   const int nloc = r1 > r0 ? (int)(r1 - r0) : 0;
@@ -257,7 +283,7 @@ __global__ void __launch_bounds__(QR_THREADS) qr_coop_kernel(const QRArgs a) {
     if (want_q && j > 0) t_column(j - 1);
     if (jl >= 0 && jl < nloc)
       for (int col = tid; col < l; col += QR_THREADS) a.pub[(size_t)j * l + col] = Yl[jl * ldy + col];
-    if (!grid_barrier(a.bar, btarget, a.err)) return;
+    if (!sync_all(a, P, btarget)) return;
     // (b) the reduced sums and row j; lane 0 of warp 0 meanwhile forms the
     // reflector's scalars from x = alpha^2 + sigma^2 with one reciprocal square
     // root and one reciprocal: beta = -sign(alpha) sqrt(x), tau = (beta -
@@ -373,7 +399,7 @@ __global__ void __launch_bounds__(QR_THREADS) qr_coop_kernel(const QRArgs a) {
     const int64_t gi = r0 + li;
     if (gi < l) a.V1g[gi * l + col] = col < gi ? Yl[li * ldy + col] : (col == gi ? 1.0 : 0.0);
   }
-  if (!grid_barrier(a.bar, btarget, a.err)) return;
+  if (!sync_all(a, P, btarget)) return;
   // K[i][x] = sum_{q = i}^{x} T[i][q] V_1[x][q] for the owned rows i, one warp per (i, x)
   for (int task = warp; task < a.nown * l; task += QR_THREADS / 32) {
     const int w = task / l, x = task % l;
@@ -385,12 +411,27 @@ __global__ void __launch_bounds__(QR_THREADS) qr_coop_kernel(const QRArgs a) {
     s = warp_sum(s);
     if (lane == 0) a.Kg[(size_t)i * l + x] = s;
   }
-  if (!grid_barrier(a.bar, btarget, a.err)) return;
+  if (!sync_all(a, P, btarget)) return;
   if (a.q_f64) {
     form_q<double>(a, Yl, ldy, (double*)qx, nloc, r0);
   } else {
     form_q<float>(a, Vf, l, (float*)qx, nloc, r0);
   }
+}
+
+__global__ void __launch_bounds__(QR_THREADS) qr_coop_kernel(const QRArgs a) {
+  qr_body(a, (int)gridDim.x, (int)blockIdx.x, false);
+}
+
+// One CTA per matrix: problem blockIdx.x of a batch.
+__global__ void __launch_bounds__(QR_THREADS) qr_batch_kernel(const QRArgs* probs) {
+  const QRArgs a = probs[blockIdx.x];
+  qr_body(a, 1, 0, true);
+}
+// The same for a single matrix, arguments by value (no host-to-device copy,
+// which from pageable memory would synchronise the stream).
+__global__ void __launch_bounds__(QR_THREADS) qr_one_kernel(const QRArgs a) {
+  qr_body(a, 1, 0, true);
 }
 
 struct QRPlan {
@@ -399,30 +440,31 @@ struct QRPlan {
 };
 
 int num_sms() {
-  static int sms = 0;
-  if (!sms) {
-    int dev = 0;
+  static const int sms = [] {
+    int dev = 0, n = 0;
     cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (sms <= 0) sms = 1;
-  }
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    return n > 0 ? n : 1;
+  }();
   return sms;
 }
 
 constexpr size_t QR_SMEM_MAX = 220 * 1024;
 
-QRPlan plan(int64_t m, int64_t l, int sms, bool want_q, bool q_f64) {
+// gm: one CTA with its rows in global memory (the batched form).
+QRPlan plan(int64_t m, int64_t l, int sms, bool want_q, bool q_f64, bool gm) {
   QRPlan p;
   const int64_t min_rows = 16;
-  int64_t P = std::min<int64_t>(sms, std::max<int64_t>(1, ceil_div(m, min_rows)));
+  int64_t P = gm ? 1 : std::min<int64_t>(sms, std::max<int64_t>(1, ceil_div(m, min_rows)));
   p.rows = (int)ceil_div(m, P);
   p.P = (int)ceil_div(m, p.rows);
   p.ldy = (int)l + 1;
   p.nown = (int)ceil_div(l, p.P);
   const bool tf = want_q && !q_f64;
-  const size_t base = ((size_t)p.rows * p.ldy + 3 * l + (size_t)QR_RPMAX * l + (size_t)p.nown * l) *
+  const size_t rows_sm = gm ? 0 : (size_t)p.rows;
+  const size_t base = (rows_sm * p.ldy + 3 * l + (size_t)QR_RPMAX * l + (size_t)p.nown * l) *
                           sizeof(double) +
-                      ((size_t)QR_RPMAX * l + p.rows + (tf ? (size_t)p.rows * l : 0)) * sizeof(float) +
+                      ((size_t)QR_RPMAX * l + rows_sm + (tf ? rows_sm * l : 0)) * sizeof(float) +
                       16;
   p.cw = 8;
   p.smem = base;
@@ -439,7 +481,108 @@ QRPlan plan(int64_t m, int64_t l, int sms, bool want_q, bool q_f64) {
 
 size_t slots_doubles(int64_t l) { return (size_t)(NREP * l * l + 4 * l * l); }
 
+// Narrow form (concurrent solves): the fewest CTAs whose row blocks fit in
+// shared memory, so that independent factorisations on other streams find
+// free SMs.
+QRPlan plan_narrow(int64_t m, int64_t l, int sms, bool want_q, bool q_f64) {
+  for (int64_t P = 1; P <= sms; ++P) {
+    QRPlan p = plan(m, l, (int)P, want_q, q_f64, false);
+    if (p.P <= P && p.smem <= QR_SMEM_MAX) return p;
+  }
+  return plan(m, l, sms, want_q, q_f64, false);
+}
+
+// Global scratch of one problem in the batched form: slots, the FP64 working
+// copy of Y and the float copies, each 256-byte aligned.
+size_t batch_problem_bytes(int64_t m, int64_t l) {
+  auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
+  return al(sizeof(double) * slots_doubles(l)) + al(sizeof(double) * m * (l + 1)) +
+         al(sizeof(float) * m * l) + al(sizeof(float) * m) + 256;
+}
+
+void fill_args(QRArgs& a, const QRProblem& pb, const QRPlan& p) {
+  a.Y = pb.Y; a.y_f64 = pb.y_f64; a.m = pb.m; a.l = pb.l; a.sr = pb.sr; a.sc = pb.sc;
+  a.Q = pb.Q; a.q_f64 = pb.q_f64; a.ldq = pb.ldq; a.R = pb.R;
+  a.rows = p.rows; a.ldy = p.ldy; a.nown = p.nown; a.cw = p.cw;
+  a.Yg = nullptr; a.Vfg = nullptr; a.yjfg = nullptr;
+}
+
+void prof_qr(int tok, cudaStream_t st, const QRProblem* pbs, int count) {
+  if (tok < 0) return;
+  // Householder factorisation 2 m l^2 - 2 l^3 / 3, explicit Q the same again
+  double fl = 0.0, by = 0.0;
+  for (int i = 0; i < count; ++i) {
+    const QRProblem& pb = pbs[i];
+    const double md = (double)pb.m, ld = (double)pb.l;
+    const double f1 = 2.0 * md * ld * ld - 2.0 * ld * ld * ld / 3.0;
+    fl += pb.Q ? 2.0 * f1 : f1;
+    by += md * ld * (pb.y_f64 ? 8 : 4) + (pb.Q ? md * ld * (pb.q_f64 ? 8 : 4) : 0.0);
+  }
+  prof_end(tok, st, fl, by);
+}
+
 }  // namespace
+
+thread_local bool g_qr_narrow = false;
+
+size_t qr_batch_workspace(int count, const int64_t* m, const int64_t* l) {
+  size_t b = 4096 + (size_t)count * sizeof(QRArgs);
+  for (int i = 0; i < count; ++i) b += batch_problem_bytes(m[i], l[i]);
+  return b;
+}
+
+void qr_f64_batched(int count, const QRProblem* pbs, void* ws, size_t ws_bytes, int* err_flag,
+                    cudaStream_t st) {
+  if (count <= 0) return;
+  for (int i = 0; i < count; ++i)
+    if (pbs[i].m < pbs[i].l || pbs[i].l <= 0) throw Error(TT_ERR_ARG, "qr_f64: need m >= l >= 1");
+  if (g_dry_run) return;
+  Arena ar(ws, ws_bytes);
+  QRArgs* dargs = ar.take<QRArgs>(count);
+  std::vector<QRArgs> hargs(count);
+  size_t smem = 0;
+  for (int i = 0; i < count; ++i) {
+    const QRProblem& pb = pbs[i];
+    const int64_t m = pb.m, l = pb.l;
+    QRPlan p = plan(m, l, 1, pb.Q != nullptr, pb.q_f64 != 0, true);
+    if (p.smem > QR_SMEM_MAX)
+      throw Error(TT_ERR_UNSUPPORTED, "qr_f64: " + std::to_string(l) +
+                                          " columns do not fit the one-CTA form");
+    smem = std::max(smem, p.smem);
+    QRArgs& a = hargs[i];
+    fill_args(a, pb, p);
+    a.acc = ar.take<double>((int64_t)slots_doubles(l));
+    a.pub = a.acc + NREP * l * l;
+    a.Tg = a.pub + l * l;
+    a.V1g = a.Tg + l * l;
+    a.Kg = a.V1g + l * l;
+    a.Yg = ar.take<double>(m * (l + 1));
+    a.Vfg = ar.take<float>(m * l);
+    a.yjfg = ar.take<float>(m);
+    a.bar = nullptr;
+    a.err = err_flag;
+  }
+  static const bool attr = [] {
+    TT_CUDA(cudaFuncSetAttribute(qr_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)QR_SMEM_MAX));
+    TT_CUDA(cudaFuncSetAttribute(qr_one_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)QR_SMEM_MAX));
+    return true;
+  }();
+  (void)attr;
+  const int tok = prof_begin(PROF_QR, st);
+  if (count == 1) {
+    qr_one_kernel<<<1, QR_THREADS, smem, st>>>(hargs[0]);
+    check_launch("qr_one_kernel");
+  } else {
+    // from pageable memory this copy completes (staged) before it returns
+    TT_CUDA(cudaMemcpyAsync(dargs, hargs.data(), sizeof(QRArgs) * count, cudaMemcpyHostToDevice,
+                            st));
+    qr_batch_kernel<<<count, QR_THREADS, smem, st>>>(dargs);
+    check_launch("qr_batch_kernel");
+  }
+  prof_qr(tok, st, pbs, count);
+}
 
 size_t qr_workspace(int64_t m, int64_t l) {
   (void)m;
@@ -452,7 +595,8 @@ void qr_f64(const void* Y, int y_f64, int64_t m, int64_t l, int64_t sr, int64_t 
   if (m < l || l <= 0) throw Error(TT_ERR_ARG, "qr_f64: need m >= l >= 1");
   if (g_dry_run) return;
   const int sms = num_sms();
-  QRPlan p = plan(m, l, sms, Q != nullptr, q_f64 != 0);
+  QRPlan p = g_qr_narrow ? plan_narrow(m, l, sms, Q != nullptr, q_f64 != 0)
+                          : plan(m, l, sms, Q != nullptr, q_f64 != 0, false);
   if (p.smem > QR_SMEM_MAX)
     throw Error(TT_ERR_UNSUPPORTED, "qr_f64: block of " + std::to_string(p.rows) + " x " +
                                         std::to_string(l) + " does not fit in shared memory");
@@ -460,34 +604,28 @@ void qr_f64(const void* Y, int y_f64, int64_t m, int64_t l, int64_t sr, int64_t 
   unsigned* bar = ar.take<unsigned>(64);
   double* slots = ar.take<double>((int64_t)slots_doubles(l));
   QRArgs a;
-  a.Y = Y; a.y_f64 = y_f64; a.m = m; a.l = l; a.sr = sr; a.sc = sc;
-  a.Q = Q; a.q_f64 = q_f64; a.ldq = ldq; a.R = R;
+  QRProblem pb{Y, y_f64, m, l, sr, sc, Q, q_f64, ldq, R};
+  fill_args(a, pb, p);
   a.acc = slots;
   a.pub = a.acc + NREP * l * l;
   a.Tg = a.pub + l * l;
   a.V1g = a.Tg + l * l;
   a.Kg = a.V1g + l * l;
-  a.bar = bar; a.err = err_flag; a.rows = p.rows; a.ldy = p.ldy; a.nown = p.nown; a.cw = p.cw;
+  a.bar = bar; a.err = err_flag;
   TT_CUDA(cudaMemsetAsync(bar, 0, 64 * sizeof(unsigned), st));
   TT_CUDA(cudaMemsetAsync(a.acc, 0, sizeof(double) * NREP * l * l, st));
-  static bool attr = false;
-  if (!attr) {
+  static const bool attr = [] {
     TT_CUDA(cudaFuncSetAttribute(qr_coop_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)QR_SMEM_MAX));
-    attr = true;
-  }
+    return true;
+  }();
+  (void)attr;
   void* args[] = {(void*)&a};
   const int tok = prof_begin(PROF_QR, st);
   TT_CUDA(cudaLaunchCooperativeKernel((const void*)qr_coop_kernel, dim3(p.P), dim3(QR_THREADS),
                                       args, p.smem, st));
   count_launch();
-  if (tok >= 0) {
-    // Householder factorisation 2 m l^2 - 2 l^3 / 3, explicit Q the same again
-    const double md = (double)m, ld = (double)l;
-    const double f1 = 2.0 * md * ld * ld - 2.0 * ld * ld * ld / 3.0;
-    prof_end(tok, st, Q ? 2.0 * f1 : f1,
-             (double)m * l * (y_f64 ? 8 : 4) + (Q ? (double)m * l * (q_f64 ? 8 : 4) : 0.0));
-  }
+  prof_qr(tok, st, &pb, 1);
 }
 
 }  // namespace ttsg

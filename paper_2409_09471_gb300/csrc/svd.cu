@@ -39,6 +39,7 @@ struct JacobiBatch {
   double* V[MAX_SVD_BATCH];
   double* sigma[MAX_SVD_BATCH];
   int* rank_out[MAX_SVD_BATCH];
+  double* vtmp[MAX_SVD_BATCH];  // V in global memory when it does not fit (else null)
 };
 
 template <typename T>
@@ -68,7 +69,9 @@ jacobi_kernel(const __grid_constant__ JacobiBatch jb, int* err) {
   double* norm_out = bi == 0 ? jb.norm_out : nullptr;
   extern __shared__ __align__(16) unsigned char sm_raw[];
   T* A = (T*)sm_raw;            // column-major: column p at A + p*l
-  T* Vm = A + (size_t)l * l;    // column-major
+  // V (column-major) in shared memory after A, or in global scratch for large l
+  T* Vm = jb.vtmp[bi] ? (T*)jb.vtmp[bi] : A + (size_t)l * l;
+  T* after = A + (size_t)l * l * (jb.vtmp[bi] ? 1 : 2);
   __shared__ int rotated;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int nthreads = blockDim.x, nwarps = nthreads / 32;
@@ -97,7 +100,7 @@ jacobi_kernel(const __grid_constant__ JacobiBatch jb, int* err) {
   const T abs_thr = tol * eps_t * tot_t;
   const int lp = l + (l & 1);   // even number of players (index l is a dummy when l is odd)
   const int npairs = lp / 2;
-  T* nrm2 = Vm + (size_t)l * l;  // squared column norms, updated with the rotations
+  T* nrm2 = after;               // squared column norms, updated with the rotations
   int sweep = 0;
   for (; sweep < MAX_SWEEPS; ++sweep) {
     // exact column norms at the start of every sweep
@@ -169,7 +172,7 @@ jacobi_kernel(const __grid_constant__ JacobiBatch jb, int* err) {
   }
   if (sweep == MAX_SWEEPS && tid == 0) atomicAdd(err, 1);  // non-convergence counter
   // column norms and descending order (ties by index)
-  double* sg = (double*)(Vm + (size_t)l * l + ((l + 1) & ~1));
+  double* sg = (double*)(after + ((l + 1) & ~1));
   for (int j = warp; j < l; j += nwarps) {
     double acc = 0.0;
     for (int i = lane; i < l; i += 32) { const double x = (double)A[(size_t)j * l + i]; acc += x * x; }
@@ -219,11 +222,22 @@ void jacobi_svd_batched(const JacobiBatchArgs& a, cudaStream_t st) {
   for (int i = 0; i < a.count; ++i) {
     jb.G[i] = a.G[i]; jb.l[i] = (int)a.l[i]; jb.GV[i] = a.GV[i]; jb.V[i] = a.V[i];
     jb.sigma[i] = a.sigma[i]; jb.rank_out[i] = a.rank_out[i];
+    jb.vtmp[i] = nullptr;
     lmax = std::max<int64_t>(lmax, a.l[i]);
   }
   const size_t es = a.f32 ? 4 : 8;
-  const size_t smem = 2 * (size_t)lmax * lmax * es + (size_t)(lmax + 2) * es +
-                      (size_t)lmax * sizeof(double) + 16;
+  const size_t tail = (size_t)(lmax + 2) * es + (size_t)lmax * sizeof(double) + 16;
+  size_t smem = 2 * (size_t)lmax * lmax * es + tail;
+  if (smem > 220 * 1024) {
+    // V moves to the callers' global scratch; A stays in shared memory
+    smem = (size_t)lmax * lmax * es + tail;
+    for (int i = 0; i < a.count; ++i) {
+      if (!a.vtmp[i])
+        throw Error(TT_ERR_UNSUPPORTED, "jacobi_svd: l = " + std::to_string(lmax) +
+                                            " needs a V scratch");
+      jb.vtmp[i] = a.vtmp[i];
+    }
+  }
   if (smem > 220 * 1024)
     throw Error(TT_ERR_UNSUPPORTED, "jacobi_svd: l = " + std::to_string(lmax) + " too large for " +
                                         (a.f32 ? "FP32" : "FP64"));
@@ -254,8 +268,9 @@ void jacobi_svd_batched(const JacobiBatchArgs& a, cudaStream_t st) {
 
 void jacobi_svd(const double* G, int64_t l, int trans, int f32, double* GV, double* V,
                 double* sigma, double eps, int64_t dm1, int64_t rmax, const double* norm_in,
-                double* norm_out, int* rank_out, int* err_flag, cudaStream_t st) {
+                double* norm_out, int* rank_out, int* err_flag, cudaStream_t st, double* vtmp) {
   JacobiBatchArgs a;
+  a.vtmp[0] = vtmp;
   a.count = 1; a.trans = trans; a.f32 = f32; a.eps = eps; a.dm1 = dm1; a.rmax = rmax;
   a.norm_in = norm_in; a.norm_out = norm_out; a.err = err_flag;
   a.G[0] = G; a.l[0] = l; a.GV[0] = GV; a.V[0] = V; a.sigma[0] = sigma; a.rank_out[0] = rank_out;

@@ -250,3 +250,14 @@ def test_bad_arguments_raise(g):
         g.tt_dot(x, dev_tt(g, ti.random_tt([4, 5], [1, 2, 1], seed=0), 0))
     with pytest.raises(g.TTError):
         g.tt_round_rand([x], [1.0], -1.0, 4, 2)
+
+
+def test_round_rand_fp64_large_bond_identity(g):
+    # a bond of 144 columns: the FP64 Jacobi SVD of the truncation keeps V in
+    # global scratch (A and V together exceed shared memory); tolerance 0
+    # must return the tensor
+    ns = [12, 12, 12, 12]
+    x = ti.random_tt(ns, [1, 12, 50, 12, 1], seed=41)
+    X = g.TT.from_numpy(x)
+    y = g.tt_round_rand([X, X, X], [1.0, 1.0, -1.0], 0.0, 150, 10, seed=3, mode=0)
+    assert tt_rel_diff(y.numpy(), x) <= 1e-12
