@@ -377,6 +377,8 @@ def run_ours(args):
                        "l2": "flushed (512 MiB write) before every step"},
             "iters_per_solve": statistics.median(iters), "true_res": info["true_res"],
             "svd_nonconverged": info.get("svd_nonconverged"),
+            "svd_sweeps": {"max": info.get("svd_max_sweeps"),
+                           "mean": round(info.get("svd_mean_sweeps") or 0.0, 2)},
             "cycles": info["cycles"], "max_rank": info["max_rank"],
             "gpu_launches": int(launches), "roofline": roof,
             "kernel_time_ms_by_class_warmup": {k: round(v["ms"], 3) for k, v in prof.items()},

@@ -292,6 +292,8 @@ typedef struct {
   int64_t* rank_hist;   /* optional host array [hist_cap]: basis max ranks */
   int hist_cap;
   int svd_nonconverged; /* small SVDs that reached their sweep cap (diagnostic) */
+  int svd_max_sweeps;   /* most Jacobi sweeps any small SVD took (diagnostic) */
+  double svd_mean_sweeps; /* mean Jacobi sweeps per small SVD (diagnostic) */
 } tt_solver_info;
 
 /*

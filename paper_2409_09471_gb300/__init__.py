@@ -274,7 +274,8 @@ def tt_sgmres_solve(op, b: TT, maxit: int, tol: float, rmax: int, mode: int = MO
     out = dict(iters=info.iters, cycles=info.cycles, sketched_res=info.sketched_res,
                true_res=info.true_res, max_rank=info.max_rank, status=info.status,
                seconds=info.seconds, res_hist=list(rh[:n]), rank_hist=list(kh[:n]),
-               svd_nonconverged=info.svd_nonconverged,
+               svd_nonconverged=info.svd_nonconverged, svd_max_sweeps=info.svd_max_sweeps,
+               svd_mean_sweeps=info.svd_mean_sweeps,
                workspace_bytes=int(need))
     return x, out
 

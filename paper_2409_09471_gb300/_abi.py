@@ -43,7 +43,8 @@ class SolverInfo(ctypes.Structure):
                 ("max_rank", ctypes.c_int64), ("status", ctypes.c_int),
                 ("seconds", ctypes.c_double), ("res_hist", ctypes.POINTER(ctypes.c_double)),
                 ("rank_hist", ctypes.POINTER(ctypes.c_int64)), ("hist_cap", ctypes.c_int),
-                ("svd_nonconverged", ctypes.c_int)]
+                ("svd_nonconverged", ctypes.c_int), ("svd_max_sweeps", ctypes.c_int),
+                ("svd_mean_sweeps", ctypes.c_double)]
 
 
 class TTError(RuntimeError):

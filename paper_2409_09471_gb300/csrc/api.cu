@@ -570,6 +570,8 @@ void do_solve(const tt_op* A, const tt_vec* b, const tt_solver_params* p, const 
     info->status = r.status;
     info->seconds = r.seconds;
     info->svd_nonconverged = r.svd_nonconverged;
+    info->svd_max_sweeps = r.svd_max_sweeps;
+    info->svd_mean_sweeps = r.svd_mean_sweeps;
     for (int i = 0; i < info->hist_cap && i < (int)r.res_hist.size(); ++i) {
       if (info->res_hist) info->res_hist[i] = r.res_hist[i];
       if (info->rank_hist) info->rank_hist[i] = r.rank_hist[i];

@@ -59,9 +59,14 @@ gemm_simt_kernel(const __grid_constant__ GemmGroup g, const __grid_constant__ Sp
   const bool a_kfast = (p.a_mode == 1) || (p.sAk == 1);
   const bool b_nfast = (p.sBn == 1);
 
-  for (int k0 = kbeg; k0 < K; k0 += BK) {
+  // global -> registers for one K tile (A: BM x BK, B: BK x BN); the next
+  // tile's loads are issued before the current tile's FMAs (register double
+  // buffering), so their latency overlaps the arithmetic
+  constexpr int RA = (BM * BK) / NT, RB = (BN * BK) / NT;
+  T ra[RA], rb[RB];
+  auto load_tile = [&](int k0) {
 #pragma unroll
-    for (int r = 0; r < (BM * BK) / NT; ++r) {
+    for (int r = 0; r < RA; ++r) {
       const int e = tid + r * NT;
       int mm, kk;
       if (a_kfast) { mm = e / BK; kk = e % BK; } else { mm = e % BM; kk = e / BM; }
@@ -76,17 +81,39 @@ gemm_simt_kernel(const __grid_constant__ GemmGroup g, const __grid_constant__ Sp
           v = A[(int64_t)m * p.sAm + (int64_t)k * p.sAk];
         }
       }
-      As[kk][mm] = v;
+      ra[r] = v;
     }
 #pragma unroll
-    for (int r = 0; r < (BN * BK) / NT; ++r) {
+    for (int r = 0; r < RB; ++r) {
       const int e = tid + r * NT;
       int nn, kk;
       if (b_nfast) { nn = e % BN; kk = e / BN; } else { nn = e / BK; kk = e % BK; }
       const int n = n0 + nn, k = k0 + kk;
-      Bs[kk][nn] = (n < N && k < K) ? B[(int64_t)k * p.sBk + (int64_t)n * p.sBn] : T(0);
+      rb[r] = (n < N && k < K) ? B[(int64_t)k * p.sBk + (int64_t)n * p.sBn] : T(0);
     }
+  };
+  auto store_tile = [&]() {
+#pragma unroll
+    for (int r = 0; r < RA; ++r) {
+      const int e = tid + r * NT;
+      int mm, kk;
+      if (a_kfast) { mm = e / BK; kk = e % BK; } else { mm = e % BM; kk = e / BM; }
+      As[kk][mm] = ra[r];
+    }
+#pragma unroll
+    for (int r = 0; r < RB; ++r) {
+      const int e = tid + r * NT;
+      int nn, kk;
+      if (b_nfast) { nn = e % BN; kk = e / BN; } else { nn = e / BK; kk = e % BK; }
+      Bs[kk][nn] = rb[r];
+    }
+  };
+
+  if (kbeg < K) load_tile(kbeg);
+  for (int k0 = kbeg; k0 < K; k0 += BK) {
+    store_tile();
     __syncthreads();
+    if (k0 + BK < K) load_tile(k0 + BK);
 #pragma unroll
     for (int kk = 0; kk < BK; ++kk) {
       T a[4], b[4];

@@ -355,9 +355,11 @@ SolveResult sgmres_solve(const Ctx& c0, const TTop<double>& A64in, const TTv<dou
     if (!g_dry_run) TT_CUDA(cudaStreamSynchronize(c.st));
   }
   if (!g_dry_run) {
-    int flags[2] = {0, 0};
+    int flags[6] = {0, 0, 0, 0, 0, 0};
     TT_CUDA(cudaMemcpy(flags, c.err, sizeof(flags), cudaMemcpyDeviceToHost));
     res.svd_nonconverged = flags[1];
+    res.svd_max_sweeps = flags[3];
+    res.svd_mean_sweeps = flags[5] > 0 ? (double)flags[4] / flags[5] : 0.0;
   }
   res.status = res.true_res <= p.tol ? TT_OK : TT_ERR_NOT_CONVERGED;
   res.seconds =

@@ -19,7 +19,8 @@ struct SolveParams {
 };
 
 struct SolveResult {
-  int iters = 0, cycles = 0, status = TT_OK, svd_nonconverged = 0;
+  int iters = 0, cycles = 0, status = TT_OK, svd_nonconverged = 0, svd_max_sweeps = 0;
+  double svd_mean_sweeps = 0.0;
   double sketched_res = 0, true_res = 0, seconds = 0;
   int64_t max_rank = 0;
   std::vector<double> res_hist;

@@ -42,17 +42,21 @@ struct JacobiBatch {
   double* vtmp[MAX_SVD_BATCH];  // V in global memory when it does not fit (else null)
 };
 
+constexpr int GL = 8;             // lanes per column pair
+constexpr int PPW = 32 / GL;      // column pairs per warp
+
 template <typename T>
-__device__ __forceinline__ T group_sum8(T v) {
-  // sum over the 8 lanes of a lane group (xor offsets 4, 2, 1)
-  v += __shfl_xor_sync(0xffffffffu, v, 4);
-  v += __shfl_xor_sync(0xffffffffu, v, 2);
-  v += __shfl_xor_sync(0xffffffffu, v, 1);
+__device__ __forceinline__ T group_sum(T v) {
+  // sum over the GL lanes of a lane group
+#pragma unroll
+  for (int o = GL / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
 }
 
-// One pair of columns per group of 8 lanes (4 pairs per warp): fewer shuffle
-// levels and a smaller block make each parallel step short.
+// One pair of columns per group of GL = 8 lanes (4 pairs per warp).  Measured
+// on GB300 at l = 74: a parallel step costs ~3K cycles, one dependent chain
+// (dot product, reduction, rotation, update) plus the block barrier; 16 lanes
+// per pair (twice the warps) was slower.
 template <typename T>
 __global__ void __launch_bounds__(SVD_THREADS)
 jacobi_kernel(const __grid_constant__ JacobiBatch jb, int* err) {
@@ -75,7 +79,7 @@ jacobi_kernel(const __grid_constant__ JacobiBatch jb, int* err) {
   __shared__ int rotated;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int nthreads = blockDim.x, nwarps = nthreads / 32;
-  const int grp = lane >> 3, sub = lane & 7;
+  const int grp = lane / GL, sub = lane % GL;
 
   for (int e = tid; e < l * l; e += nthreads) {
     const int i = e / l, j = e % l;           // element (i, j) of G
@@ -113,7 +117,7 @@ jacobi_kernel(const __grid_constant__ JacobiBatch jb, int* err) {
     if (tid == 0) rotated = 0;
     __syncthreads();
     for (int step = 0; step < lp - 1; ++step) {
-      for (int k0 = warp * 4; k0 < npairs; k0 += nwarps * 4) {
+      for (int k0 = warp * PPW; k0 < npairs; k0 += nwarps * PPW) {
         const int k = k0 + grp;
         int p = -1, q = -1;
         if (k < npairs) {
@@ -124,11 +128,19 @@ jacobi_kernel(const __grid_constant__ JacobiBatch jb, int* err) {
         }
         T ga = 0;
         if (p >= 0) {
+          // two independent chains per lane (the loop is latency-bound)
           const T* ap = A + (size_t)p * l;
           const T* aq = A + (size_t)q * l;
-          for (int i = sub; i < l; i += 8) ga += ap[i] * aq[i];
+          T g0 = 0, g1 = 0;
+          int i = sub;
+          for (; i + GL < l; i += 2 * GL) {
+            g0 = fma(ap[i], aq[i], g0);
+            g1 = fma(ap[i + GL], aq[i + GL], g1);
+          }
+          if (i < l) g0 = fma(ap[i], aq[i], g0);
+          ga = g0 + g1;
         }
-        ga = group_sum8(ga);
+        ga = group_sum(ga);
         if (p < 0) continue;
         const T al = nrm2[p], be = nrm2[q];
         // converged pair: relative test, or an inner product at the rounding
@@ -152,7 +164,21 @@ jacobi_kernel(const __grid_constant__ JacobiBatch jb, int* err) {
         T* aq = A + (size_t)q * l;
         T* vp = Vm + (size_t)p * l;
         T* vq = Vm + (size_t)q * l;
-        for (int i = sub; i < l; i += 8) {
+        int i = sub;
+        for (; i + GL < l; i += 2 * GL) {
+          // two rows per iteration, all loads before the stores
+          const T x0 = ap[i], y0 = aq[i], u0 = vp[i], w0 = vq[i];
+          const T x1 = ap[i + GL], y1 = aq[i + GL], u1 = vp[i + GL], w1 = vq[i + GL];
+          ap[i] = c * x0 - s * y0;
+          aq[i] = s * x0 + c * y0;
+          vp[i] = c * u0 - s * w0;
+          vq[i] = s * u0 + c * w0;
+          ap[i + GL] = c * x1 - s * y1;
+          aq[i + GL] = s * x1 + c * y1;
+          vp[i + GL] = c * u1 - s * w1;
+          vq[i + GL] = s * u1 + c * w1;
+        }
+        if (i < l) {
           const T x = ap[i], y = aq[i], u = vp[i], w = vq[i];
           ap[i] = c * x - s * y;
           aq[i] = s * x + c * y;
@@ -170,7 +196,13 @@ jacobi_kernel(const __grid_constant__ JacobiBatch jb, int* err) {
     if (!rotated) break;
     __syncthreads();
   }
-  if (sweep == MAX_SWEEPS && tid == 0) atomicAdd(err, 1);  // non-convergence counter
+  if (tid == 0) {
+    if (sweep == MAX_SWEEPS) atomicAdd(err, 1);  // non-convergence counter
+    // sweep statistics: err[2] maximum, err[3] total, err[4] problems
+    atomicMax(err + 2, sweep);
+    atomicAdd(err + 3, sweep);
+    atomicAdd(err + 4, 1);
+  }
   // column norms and descending order (ties by index)
   double* sg = (double*)(after + ((l + 1) & ~1));
   for (int j = warp; j < l; j += nwarps) {
@@ -242,10 +274,10 @@ void jacobi_svd_batched(const JacobiBatchArgs& a, cudaStream_t st) {
     throw Error(TT_ERR_UNSUPPORTED, "jacobi_svd: l = " + std::to_string(lmax) + " too large for " +
                                         (a.f32 ? "FP32" : "FP64"));
   static bool attr[2] = {false, false};
-  // 4 column pairs per warp
+  // PPW column pairs per warp
   const int pairs = (int)((lmax + 1) / 2);
   const int threads =
-      (int)std::min<int64_t>(SVD_THREADS, std::max<int64_t>(64, ceil_div(pairs, 4) * 32));
+      (int)std::min<int64_t>(SVD_THREADS, std::max<int64_t>(64, ceil_div(pairs, PPW) * 32));
   const int tok = prof_begin(PROF_SVD, st);
   if (a.f32) {
     if (!attr[0]) {
