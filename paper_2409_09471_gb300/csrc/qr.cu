@@ -165,8 +165,9 @@ __device__ __forceinline__ void qr_body(const QRArgs& a, int P, int c, bool gm) 
   // float Q: the compact-WY products (columns < j) run on the FP32 pipe from a
   // float copy of the normalised reflectors (also the V operand of form_q)
   const bool tf = want_q && !a.q_f64;
+  const int64_t r0 = (int64_t)c * a.rows;                // first row of this CTA
   double* sp = smem;
-  double* Yl = gm ? a.Yg : sp;                           // [rows][ldy]: R above, v below
+  double* Yl = gm ? a.Yg + r0 * ldy : sp;                // [rows][ldy]: R above, v below
   if (!gm) sp += (size_t)a.rows * ldy;
   double* ts = sp;                                       // [l] reduced sums t_c
   double* rj = ts + l;                                   // [l] published row j
@@ -175,20 +176,19 @@ __device__ __forceinline__ void qr_body(const QRArgs& a, int P, int c, bool gm) 
   double* Tl = part + (size_t)QR_RPMAX * l;              // [nown][l] owned rows of T
   float* partf = (float*)(Tl + (size_t)a.nown * l);      // [QR_RPMAX][l]
   float* fp = partf + (size_t)QR_RPMAX * l;
-  float* yjf = gm ? a.yjfg : fp;                         // [rows] column j in float
+  float* yjf = gm ? a.yjfg + r0 : fp;                    // [rows] column j in float
   if (!gm) fp += a.rows;
-  float* Vf = gm ? a.Vfg : fp;                           // [rows][l] reflectors in float
+  float* Vf = gm ? a.Vfg + r0 * l : fp;                  // [rows][l] reflectors in float
   if (!gm && tf) fp += (size_t)a.rows * l;
   unsigned char* qx =                                    // Q-formation chunk, 16-byte aligned
       (unsigned char*)(((uintptr_t)fp + 15) & ~(uintptr_t)15);
   __shared__ double hs[4];  // beta, tau, scale of the current reflector
   unsigned btarget = 0;  // running grid-barrier target (used by thread 0)
-  if (gm) {
+  if (gm && P == 1) {
     // one CTA: its own reduction slots are cleared here instead of by the host
     for (int e = tid; e < NREP * l * l; e += QR_THREADS) a.acc[e] = 0.0;
     __syncthreads();
   }
-  const int64_t r0 = (int64_t)c * a.rows;
   const int64_t r1 = a.m < r0 + a.rows ? a.m : r0 + a.rows;
   const int nloc = r1 > r0 ? (int)(r1 - r0) : 0;
 
@@ -422,6 +422,11 @@ __device__ __forceinline__ void qr_body(const QRArgs& a, int P, int c, bool gm) 
 __global__ void __launch_bounds__(QR_THREADS) qr_coop_kernel(const QRArgs a) {
   qr_body(a, (int)gridDim.x, (int)blockIdx.x, false);
 }
+// The same with the row blocks in global memory (matrices whose row blocks do
+// not fit in shared memory).
+__global__ void __launch_bounds__(QR_THREADS) qr_coop_gm_kernel(const QRArgs a) {
+  qr_body(a, (int)gridDim.x, (int)blockIdx.x, true);
+}
 
 // One CTA per matrix: problem blockIdx.x of a batch.
 __global__ void __launch_bounds__(QR_THREADS) qr_batch_kernel(const QRArgs* probs) {
@@ -451,11 +456,12 @@ int num_sms() {
 
 constexpr size_t QR_SMEM_MAX = 220 * 1024;
 
-// gm: one CTA with its rows in global memory (the batched form).
+// gm: the row blocks and their float copies live in global memory (the
+// batched one-CTA form, and matrices whose row blocks exceed shared memory).
 QRPlan plan(int64_t m, int64_t l, int sms, bool want_q, bool q_f64, bool gm) {
   QRPlan p;
   const int64_t min_rows = 16;
-  int64_t P = gm ? 1 : std::min<int64_t>(sms, std::max<int64_t>(1, ceil_div(m, min_rows)));
+  int64_t P = std::min<int64_t>(sms, std::max<int64_t>(1, ceil_div(m, min_rows)));
   p.rows = (int)ceil_div(m, P);
   p.P = (int)ceil_div(m, p.rows);
   p.ldy = (int)l + 1;
@@ -584,9 +590,26 @@ void qr_f64_batched(int count, const QRProblem* pbs, void* ws, size_t ws_bytes, 
   prof_qr(tok, st, pbs, count);
 }
 
+// The shared-memory plan does not fit for some precision pair: the rows go to
+// global memory (an FP64 copy of Y, float copies of the reflectors and of the
+// current column).
+static bool needs_global_rows(int64_t m, int64_t l) {
+  const int sms = num_sms();
+  for (int want_q = 0; want_q < 2; ++want_q)
+    for (int q64 = 0; q64 < 2; ++q64) {
+      const QRPlan p = g_qr_narrow ? plan_narrow(m, l, sms, want_q, q64)
+                                   : plan(m, l, sms, want_q, q64, false);
+      if (p.smem > QR_SMEM_MAX) return true;
+    }
+  return false;
+}
+static size_t global_rows_bytes(int64_t m, int64_t l) {
+  return sizeof(double) * m * (l + 1) + sizeof(float) * m * l + sizeof(float) * m + 3 * 256;
+}
+
 size_t qr_workspace(int64_t m, int64_t l) {
-  (void)m;
-  return 2048 + sizeof(double) * slots_doubles(l);
+  return 2048 + sizeof(double) * slots_doubles(l) +
+         (needs_global_rows(m, l) ? global_rows_bytes(m, l) : 0);
 }
 
 void qr_f64(const void* Y, int y_f64, int64_t m, int64_t l, int64_t sr, int64_t sc, void* Q,
@@ -597,15 +620,26 @@ void qr_f64(const void* Y, int y_f64, int64_t m, int64_t l, int64_t sr, int64_t 
   const int sms = num_sms();
   QRPlan p = g_qr_narrow ? plan_narrow(m, l, sms, Q != nullptr, q_f64 != 0)
                           : plan(m, l, sms, Q != nullptr, q_f64 != 0, false);
+  bool gm = false;
+  if (p.smem > QR_SMEM_MAX) {
+    // row blocks too large for shared memory: keep them in global memory
+    p = plan(m, l, sms, Q != nullptr, q_f64 != 0, true);
+    gm = true;
+  }
   if (p.smem > QR_SMEM_MAX)
-    throw Error(TT_ERR_UNSUPPORTED, "qr_f64: block of " + std::to_string(p.rows) + " x " +
-                                        std::to_string(l) + " does not fit in shared memory");
+    throw Error(TT_ERR_UNSUPPORTED, "qr_f64: " + std::to_string(l) +
+                                        " columns do not fit in shared memory");
   Arena ar(ws, ws_bytes);
   unsigned* bar = ar.take<unsigned>(64);
   double* slots = ar.take<double>((int64_t)slots_doubles(l));
   QRArgs a;
   QRProblem pb{Y, y_f64, m, l, sr, sc, Q, q_f64, ldq, R};
   fill_args(a, pb, p);
+  if (gm) {
+    a.Yg = ar.take<double>(m * (l + 1));
+    a.Vfg = ar.take<float>(m * l);
+    a.yjfg = ar.take<float>(m);
+  }
   a.acc = slots;
   a.pub = a.acc + NREP * l * l;
   a.Tg = a.pub + l * l;
@@ -617,13 +651,16 @@ void qr_f64(const void* Y, int y_f64, int64_t m, int64_t l, int64_t sr, int64_t 
   static const bool attr = [] {
     TT_CUDA(cudaFuncSetAttribute(qr_coop_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)QR_SMEM_MAX));
+    TT_CUDA(cudaFuncSetAttribute(qr_coop_gm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)QR_SMEM_MAX));
     return true;
   }();
   (void)attr;
   void* args[] = {(void*)&a};
   const int tok = prof_begin(PROF_QR, st);
-  TT_CUDA(cudaLaunchCooperativeKernel((const void*)qr_coop_kernel, dim3(p.P), dim3(QR_THREADS),
-                                      args, p.smem, st));
+  TT_CUDA(cudaLaunchCooperativeKernel(gm ? (const void*)qr_coop_gm_kernel
+                                         : (const void*)qr_coop_kernel,
+                                      dim3(p.P), dim3(QR_THREADS), args, p.smem, st));
   count_launch();
   prof_qr(tok, st, &pb, 1);
 }

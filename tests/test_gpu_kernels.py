@@ -261,3 +261,21 @@ def test_round_rand_fp64_large_bond_identity(g):
     X = g.TT.from_numpy(x)
     y = g.tt_round_rand([X, X, X], [1.0, 1.0, -1.0], 0.0, 150, 10, seed=3, mode=0)
     assert tt_rel_diff(y.numpy(), x) <= 1e-12
+
+
+@pytest.mark.parametrize("m,l", [(33792, 264), (6000, 200)])
+def test_qr_f64_wide_rows_in_global_memory(g, m, l):
+    # row blocks too large for shared memory: the cooperative factorisation
+    # keeps them in global memory (the exact residual check of a rank-128 TT
+    # with a rank-8 right-hand side factorises 264 columns)
+    rng = np.random.default_rng(m + l)
+    Y = rng.standard_normal((m, l))
+    Y[:, 5] = Y[:, 3]
+    Yd = torch.as_tensor(Y, device="cuda")
+    Q, R = g.tt_qr_f64(Yd)
+    Q, R = Q.cpu().numpy(), R.cpu().numpy()
+    assert np.max(np.abs(Q.T @ Q - np.eye(l))) <= 1e-13 * l
+    assert np.max(np.abs(Q @ R - Y)) <= 1e-13 * np.max(np.abs(Y)) * l
+    Qf, _ = g.tt_qr_f64(Yd.float())
+    Qf = Qf.cpu().double().numpy()
+    assert np.max(np.abs(Qf.T @ Qf - np.eye(l))) <= 1e-6 * l
