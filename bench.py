@@ -87,6 +87,19 @@ def peaks():
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
 
 
+def max_over_ranks(value: float, device="cpu") -> float:
+    """The slowest rank's timed interval (replicas: every rank solves its own
+    copy, so the job takes as long as the slowest one).  Returns ``value``
+    unchanged without an initialised process group."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 # ---------------------------------------------------------------- clocks
 class Clocks:
     QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -284,11 +297,7 @@ def run_ours(args):
     barrier()
     clk = clocks.stop()
     launches = lib.tt_launch_count() - launches0
-    total_ms = sum(times)
-    if world > 1:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = t.item()
+    total_ms = max_over_ranks(sum(times), "cuda")
     ms, nl, fl, by = ctypes.c_double(), ctypes.c_int64(), ctypes.c_double(), ctypes.c_double()
     lib.tt_profile_read(dom_cls, ctypes.byref(ms), ctypes.byref(nl), ctypes.byref(fl), ctypes.byref(by))
     lib.tt_profile(0)
