@@ -30,6 +30,16 @@
 // float, that product runs on the FP32 pipe (K and V rounded to float,
 // accumulation in blocks of 8); in FP64 it stays in FP64.
 //
+// Forms of the same factorisation body (qr_body):
+//  * cooperative (qr_coop_kernel): up to one CTA per SM, row blocks in shared
+//    memory; the single-solve default;
+//  * narrow: the fewest CTAs whose row blocks fit in shared memory, used when
+//    many independent solves share the GPU (g_qr_narrow);
+//  * global rows (qr_coop_gm_kernel): row blocks too large for shared memory
+//    stay in global memory (L2), everything else unchanged;
+//  * batched (qr_batch_kernel / qr_one_kernel): one CTA per matrix with its
+//    rows in global memory, many matrices in one launch.
+//
 // Grid barriers spin a bounded number of times; on expiry the kernel sets bit 0
 // of the error flag and every CTA returns (the host reports TT_ERR_TIMEOUT).
 #include "kernels.cuh"
