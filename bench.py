@@ -258,13 +258,13 @@ def run_ours(args):
     info = None
     for i in range(args.warmup):
         if i == args.warmup - 1:
-            lib.tt_profile(0x7F)
+            lib.tt_profile(0xFF)
         x, info = g.tt_sgmres_solve(op, b, mode=mode, workspace=ws, **kw)
         if ws is None:
             ws = torch.empty(info["workspace_bytes"], dtype=torch.uint8, device="cuda")
     torch.cuda.synchronize()
     classes = {0: "gemm", 1: "qr_f64", 2: "jacobi_svd", 3: "lstsq", 4: "misc", 5: "gram_f64",
-               6: "chol_f64"}
+               6: "chol_f64", 7: "tc_matvec"}
     prof = {}
     for cl in classes:
         ms, nl, fl, by = ctypes.c_double(), ctypes.c_int64(), ctypes.c_double(), ctypes.c_double()
@@ -377,6 +377,20 @@ def run_ours(args):
         e2e_ms.append(e0.elapsed_time(e1))
         d2h = sum(o.numel() * o.element_size() for o in outs)
 
+    # the contraction half of the metric: algorithmic TFLOP/s of the tcgen05
+    # matvec (against the TF32 tensor peak; the split-TF32 scheme issues three
+    # products per algorithmic one) and of the CUDA-core GEMMs (against the FP32
+    # unit peak), from the profiled warm-up step
+    contraction = {}
+    for key, peak_c, kind in (("tc_matvec", pk["bf16_tflops_sustained"] * TF32_OVER_BF16,
+                               f"{pk_kind} BF16 sustained x 1.1/2.25 (TF32 tensor)"),
+                              ("gemm", FP32_ALU_TFLOPS, "FP32 CUDA-core peak from unit counts")):
+        v = prof[key]
+        if v["ms"] > 0 and v["launches"] > 0:
+            tf = v["flops"] / (v["ms"] * 1e-3) / 1e12
+            contraction[key] = {"tflops": tf, "peak": peak_c, "frac": tf / peak_c,
+                                "peak_kind": kind, "launches": v["launches"],
+                                "avg_launch_us": v["ms"] * 1e3 / v["launches"]}
     line = {"metric": METRIC, "value": value, "unit": "s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None,
@@ -389,7 +403,7 @@ def run_ours(args):
             "svd_sweeps": {"max": info.get("svd_max_sweeps"),
                            "mean": round(info.get("svd_mean_sweeps") or 0.0, 2)},
             "cycles": info["cycles"], "max_rank": info["max_rank"],
-            "gpu_launches": int(launches), "roofline": roof,
+            "gpu_launches": int(launches), "roofline": roof, "contraction": contraction,
             "kernel_time_ms_by_class_warmup": {k: round(v["ms"], 3) for k, v in prof.items()},
             "e2e": {"value": statistics.mean(e2e_ms) / 1e3, "unit": "s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},

@@ -135,8 +135,13 @@ void gemm(int mode, const std::vector<GemmProblem>& probs, cudaStream_t st);
 // operator core Dp ([R0][n R1][n]) and the transposed vector core Ct
 // ([r0][r1][n]); float data, n a multiple of 4 (tensor-map row alignment).
 bool matvec_tc_supported(int64_t n, int64_t r1);
-void matvec_core_tc(const float* Dp, const float* Ct, float* G, int64_t n, int64_t R0, int64_t R1,
-                    int64_t r0, int64_t r1, int* err, cudaStream_t st);
+struct TcCoreArgs {
+  const float* Dp;  // working-layout operator core [R0][n R1][n]
+  const float* Ct;  // transposed vector core [r0][r1][n]
+  float* G;         // output core
+  int64_t n, R0, R1, r0, r1;
+};
+void matvec_tc_cores(const std::vector<TcCoreArgs>& cores, int* err, cudaStream_t st);
 // Device scratch for split-K partial sums (set per API call; null disables split-K).
 void set_gemm_scratch(void* ws, size_t bytes);
 constexpr size_t GEMM_SCRATCH_BYTES = size_t(48) << 20;

@@ -97,12 +97,23 @@ __host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
          | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
-struct MatvecTC {
+// One core of the matvec: the operator slices (A operand) and the transposed
+// vector core (B operand) as tensor maps, with the core's GEMM sizes.
+struct TcCore {
+  CUtensorMap mA, mB;
   int M;        // n * R1 rows of one operator slice (i, a')
   int N;        // r1
   int K;        // n
   int r0, R0;   // batch: a in [0, R0), l in [0, r0)
   float* G;     // output core
+};
+// All cores of one matvec in one launch: blockIdx.z selects the core,
+// blockIdx.y the batch entry (a, l), blockIdx.x the output tile; entries past a
+// core's own extent exit before any setup.
+constexpr int TC_MAXC = 16;
+struct TcBatch {
+  TcCore c[TC_MAXC];
+  int count;
   int* err;
 };
 
@@ -123,8 +134,11 @@ __device__ __forceinline__ void split_tf32(float* hi, float* lo, int count) {
 }
 
 __global__ void __launch_bounds__(TC_THREADS, 1)
-matvec_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
-                 const MatvecTC p) {
+matvec_tc_kernel(const __grid_constant__ TcBatch b) {
+  if ((int)blockIdx.z >= b.count) return;
+  const TcCore& p = b.c[blockIdx.z];
+  const CUtensorMap& mapA = p.mA;
+  const CUtensorMap& mapB = p.mB;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   // 1024-byte aligned tiles for the 128-byte swizzle: [A hi | B hi | A lo | B lo]
   unsigned char* base =
@@ -140,7 +154,7 @@ matvec_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant
 
   const int tiles_m = (p.M + TM - 1) / TM, tiles_n = (p.N + TN - 1) / TN;
   const int tm = blockIdx.x % tiles_m, tn = blockIdx.x / tiles_m;
-  if (tn >= tiles_n) return;
+  if (tn >= tiles_n || (int)blockIdx.y >= p.R0 * p.r0) return;
   const int a = blockIdx.y / p.r0, l = blockIdx.y % p.r0;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
@@ -215,7 +229,7 @@ matvec_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant
   }
   if (stage != 0 && threadIdx.x == 0) {
     fail = 1;
-    atomicOr(p.err, 4);
+    atomicOr(b.err, 4);
     // let copies or MMAs still in flight land before the CTA leaves
     mbar_wait(&bar_full, phase);
     if (stage == 2) mbar_wait(&bar_mma, phase);
@@ -295,28 +309,46 @@ bool matvec_tc_supported(int64_t n, int64_t r1) {
   return (n % 4) == 0 && n >= 8 && r1 >= 1;
 }
 
-// One core: G (R0 r0 x n x R1 r1) from Dp ([R0][n R1][n]) and Ct ([r0][r1][n]).
-void matvec_core_tc(const float* Dp, const float* Ct, float* G, int64_t n, int64_t R0, int64_t R1,
-                    int64_t r0, int64_t r1, int* err, cudaStream_t st) {
-  if (g_dry_run) return;
-  const int64_t M = n * R1;
-  CUtensorMap mA = make_map(Dp, n, R0 * M, n, TM);
-  CUtensorMap mB = make_map(Ct, n, r0 * r1, n, TN);
-  MatvecTC p;
-  p.M = (int)M; p.N = (int)r1; p.K = (int)n; p.r0 = (int)r0; p.R0 = (int)R0; p.G = G; p.err = err;
-  const int tiles = (int)(ceil_div(M, TM) * ceil_div(r1, TN));
+// All tensor-core cores of one matvec: core k gives G_k (R0 r0 x n x R1 r1)
+// from Dp_k ([R0][n R1][n]) and Ct_k ([r0][r1][n]); up to TC_MAXC cores per
+// launch.
+void matvec_tc_cores(const std::vector<TcCoreArgs>& cores, int* err, cudaStream_t st) {
+  if (g_dry_run || cores.empty()) return;
   const size_t smem = (size_t)2 * (TM + TN) * TK * 4 + 1024;
-  static bool attr = false;
-  if (!attr) {
+  static const bool attr = [smem] {
     TT_CUDA(cudaFuncSetAttribute(matvec_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)smem));
-    attr = true;
+    return true;
+  }();
+  (void)attr;
+  for (size_t c0 = 0; c0 < cores.size(); c0 += TC_MAXC) {
+    TcBatch bt;
+    bt.count = 0;
+    bt.err = err;
+    int64_t max_tiles = 1, max_batch = 1;
+    double flops = 0.0, bytes = 0.0;
+    for (size_t i = c0; i < cores.size() && bt.count < TC_MAXC; ++i) {
+      const TcCoreArgs& q = cores[i];
+      const int64_t M = q.n * q.R1;
+      TcCore& cc = bt.c[bt.count++];
+      cc.mA = make_map(q.Dp, q.n, q.R0 * M, q.n, TM);
+      cc.mB = make_map(q.Ct, q.n, q.r0 * q.r1, q.n, TN);
+      cc.M = (int)M; cc.N = (int)q.r1; cc.K = (int)q.n; cc.r0 = (int)q.r0; cc.R0 = (int)q.R0;
+      cc.G = q.G;
+      max_tiles = std::max(max_tiles, ceil_div(M, (int64_t)TM) * ceil_div(q.r1, (int64_t)TN));
+      max_batch = std::max(max_batch, q.R0 * q.r0);
+      flops += 2.0 * M * q.r1 * q.n * q.R0 * q.r0;
+      bytes += 4.0 * (q.R0 * M * q.n + q.r0 * q.r1 * q.n + q.R0 * q.r0 * M * q.r1);
+    }
+    if (max_batch > 65535) throw Error(TT_ERR_UNSUPPORTED, "matvec_tc: batch too large");
+    const int tok = prof_begin(PROF_TC, st);
+    matvec_tc_kernel<<<dim3((unsigned)max_tiles, (unsigned)max_batch, (unsigned)bt.count),
+                       TC_THREADS, smem, st>>>(bt);
+    check_launch("matvec_tc_kernel");
+    // algorithmic flops and bytes (one product; the split adds two more on
+    // the tensor pipe)
+    prof_end(tok, st, flops, bytes);
   }
-  const int tok = prof_begin(PROF_GEMM, st);
-  matvec_tc_kernel<<<dim3(tiles, (unsigned)(R0 * r0)), TC_THREADS, smem, st>>>(mA, mB, p);
-  check_launch("matvec_tc_kernel");
-  prof_end(tok, st, 2.0 * M * r1 * n * R0 * r0,  // algorithmic flops (one product)
-           4.0 * (R0 * M * n + r0 * r1 * n + R0 * r0 * M * r1));
 }
 
 // Grouped GEMMs other than the matvec run on the FP32 CUDA-core kernel in

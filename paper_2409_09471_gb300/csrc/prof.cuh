@@ -7,7 +7,7 @@
 namespace ttsg {
 
 enum ProfClass { PROF_GEMM = 0, PROF_QR = 1, PROF_SVD = 2, PROF_LSTSQ = 3, PROF_MISC = 4,
-                 PROF_GRAM = 5, PROF_CHOL = 6, PROF_NCLASS = 7 };
+                 PROF_GRAM = 5, PROF_CHOL = 6, PROF_TC = 7, PROF_NCLASS = 8 };
 
 bool prof_on(int cls);
 // Counts every kernel launch the library enqueues (read by tt_launch_count).

@@ -50,8 +50,11 @@ template <typename T>
 void tt_matvec_dev(const Ctx& c, const TTop<T>& A, const TTv<T>& x, const TTv<T>& y) {
   std::vector<GemmProblem> ps;
   if (c.mode == TT_MODE_TF32 && sizeof(T) == 4) {
-    // tensor cores: per core, Ct[l][l'][j] = C[l][j][l'] then the tcgen05 GEMM
+    // tensor cores: Ct_k[l][l'][j] = C_k[l][j][l'] for every core (one copy
+    // launch), then one tcgen05 launch for all of them
     const size_t mk = c.ar->mark();
+    std::vector<CopySeg> segs;
+    std::vector<TcCoreArgs> tc;
     for (int k = 0; k < x.d; ++k) {
       const int64_t n = x.n[k], R0 = A.R[k], R1 = A.R[k + 1], r0 = x.r[k], r1 = x.r[k + 1];
       if (!matvec_tc_supported(n, r1)) continue;
@@ -59,10 +62,11 @@ void tt_matvec_dev(const Ctx& c, const TTop<T>& A, const TTv<T>& x, const TTv<T>
       CopySeg sg;
       sg.src = x.core[k]; sg.dst = Ct; sg.A = r0; sg.B = r1; sg.C = n;
       sg.sa = n * r1; sg.sb = 1; sg.sc = r1;
-      copy3d({sg}, c.st);
-      matvec_core_tc((const float*)A.core[k], Ct, (float*)y.core[k], n, R0, R1, r0, r1, c.err,
-                     c.st);
+      segs.push_back(sg);
+      tc.push_back(TcCoreArgs{(const float*)A.core[k], Ct, (float*)y.core[k], n, R0, R1, r0, r1});
     }
+    copy3d(segs, c.st);
+    matvec_tc_cores(tc, c.err, c.st);
     c.ar->release(mk);
     for (int k = 0; k < x.d; ++k) {
       if (matvec_tc_supported(x.n[k], x.r[k + 1])) continue;
