@@ -238,10 +238,15 @@ matvec_tc_kernel(const __grid_constant__ TcBatch b) {
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 
+  // epilogue: warp w owns accumulator lanes (rows) 32w .. 32w+31.  The tile
+  // goes through shared memory (the operand tiles are free now; row stride
+  // TN + 1 keeps a warp's per-row writes in distinct banks) and then to the
+  // output row by row, so that consecutive threads store consecutive columns.
+  float* St = (float*)base;
+  constexpr int LDS = TN + 1;
+  static_assert(TM * LDS * 4 <= 2 * (TM + TN) * TK * 4, "staging tile exceeds the operand tiles");
   if (!fail) {
-    // epilogue: warp w owns accumulator lanes (rows) 32w .. 32w+31
-    const int m = tm * TM + warp * 32 + lane;
-    const int64_t out_base = ((int64_t)(a * p.r0 + l) * p.M + m) * p.N;
+    const int row = warp * 32 + lane;
 #pragma unroll
     for (int c0 = 0; c0 < TN; c0 += 16) {
       uint32_t r[16];
@@ -254,13 +259,17 @@ matvec_tc_kernel(const __grid_constant__ TcBatch b) {
             "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
           : "r"(taddr));
       asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-      if (m < p.M) {
 #pragma unroll
-        for (int q = 0; q < 16; ++q) {
-          const int n = tn * TN + c0 + q;
-          if (n < p.N) p.G[out_base + n] = __uint_as_float(r[q]);
-        }
-      }
+      for (int q = 0; q < 16; ++q) St[row * LDS + c0 + q] = __uint_as_float(r[q]);
+    }
+  }
+  __syncthreads();
+  if (!fail) {
+    const int64_t gbase = (int64_t)(a * p.r0 + l) * p.M * p.N;
+    for (int e = threadIdx.x; e < TM * TN; e += TC_THREADS) {
+      const int rr = e / TN, cc = e % TN;
+      const int m = tm * TM + rr, n = tn * TN + cc;
+      if (m < p.M && n < p.N) p.G[gbase + (int64_t)m * p.N + n] = St[rr * LDS + cc];
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");

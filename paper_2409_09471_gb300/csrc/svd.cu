@@ -121,8 +121,15 @@ jacobi_kernel(const __grid_constant__ JacobiBatch jb, int* err) {
         const int k = k0 + grp;
         int p = -1, q = -1;
         if (k < npairs) {
+          // round-robin pairing: player lp-1 stays, the others rotate (no
+          // integer division: 0 <= step < lp-1 and 0 < k < lp/2)
           if (k == 0) { p = lp - 1; q = step; }
-          else { p = (step + k) % (lp - 1); q = (step - k + (lp - 1)) % (lp - 1); }
+          else {
+            p = step + k;
+            if (p >= lp - 1) p -= lp - 1;
+            q = step - k;
+            if (q < 0) q += lp - 1;
+          }
           if (p >= l || q >= l) p = q = -1;
           else if (p > q) { const int t = p; p = q; q = t; }
         }
