@@ -92,7 +92,11 @@ void chol_f64_batched(int count, const double* const* G, const int64_t* l, doubl
 // A sweep cap reached without convergence increments *err_flag.
 void jacobi_svd(const double* G, int64_t l, int trans, int f32, double* GV, double* V, double* sigma,
                 double eps, int64_t dm1, int64_t rmax, const double* norm_in, double* norm_out,
-                int* rank_out, int* err_flag, cudaStream_t st, double* vtmp = nullptr);
+                int* rank_out, int* err_flag, cudaStream_t st, double* vtmp = nullptr,
+                double* pre = nullptr);
+// (pre: 4 l x l doubles of scratch; with f32 == 0 the FP64 result is then
+// reached by an FP32 pass, an FP64 re-orthogonalisation of its rotations and
+// FP64 sweeps from them)
 
 // Batched form: one CTA per problem; every problem uses the same rank rule
 // parameters.  With norm_in == nullptr each problem takes its own sqrt(sum
@@ -111,6 +115,7 @@ struct JacobiBatchArgs {
   double* sigma[TT_MAX_D] = {};
   int* rank_out[TT_MAX_D] = {};
   double* vtmp[TT_MAX_D] = {};  // l x l scratch each, used when l is too large for shared memory
+  const double* v0[TT_MAX_D] = {};  // initial rotations (row-major l x l), null = identity
 };
 void jacobi_svd_batched(const JacobiBatchArgs& a, cudaStream_t st);
 

@@ -40,6 +40,7 @@ struct JacobiBatch {
   double* sigma[MAX_SVD_BATCH];
   int* rank_out[MAX_SVD_BATCH];
   double* vtmp[MAX_SVD_BATCH];  // V in global memory when it does not fit (else null)
+  const double* v0[MAX_SVD_BATCH];  // initial rotations, row-major (else the identity)
 };
 
 constexpr int GL = 8;             // lanes per column pair
@@ -84,7 +85,7 @@ jacobi_kernel(const __grid_constant__ JacobiBatch jb, int* err) {
   for (int e = tid; e < l * l; e += nthreads) {
     const int i = e / l, j = e % l;           // element (i, j) of G
     A[(size_t)j * l + i] = (T)(trans ? G[(size_t)j * l + i] : G[e]);
-    Vm[(size_t)j * l + i] = (i == j) ? T(1) : T(0);
+    Vm[(size_t)j * l + i] = jb.v0[bi] ? (T)jb.v0[bi][e] : ((i == j) ? T(1) : T(0));
   }
   __syncthreads();
   const T eps_t = sizeof(T) == 4 ? (T)1.1920929e-07 : (T)2.220446049250313e-16;
@@ -262,6 +263,7 @@ void jacobi_svd_batched(const JacobiBatchArgs& a, cudaStream_t st) {
     jb.G[i] = a.G[i]; jb.l[i] = (int)a.l[i]; jb.GV[i] = a.GV[i]; jb.V[i] = a.V[i];
     jb.sigma[i] = a.sigma[i]; jb.rank_out[i] = a.rank_out[i];
     jb.vtmp[i] = nullptr;
+    jb.v0[i] = a.v0[i];
     lmax = std::max<int64_t>(lmax, a.l[i]);
   }
   const size_t es = a.f32 ? 4 : 8;
@@ -307,13 +309,57 @@ void jacobi_svd_batched(const JacobiBatchArgs& a, cudaStream_t st) {
 
 void jacobi_svd(const double* G, int64_t l, int trans, int f32, double* GV, double* V,
                 double* sigma, double eps, int64_t dm1, int64_t rmax, const double* norm_in,
-                double* norm_out, int* rank_out, int* err_flag, cudaStream_t st, double* vtmp) {
+                double* norm_out, int* rank_out, int* err_flag, cudaStream_t st, double* vtmp,
+                double* pre) {
   JacobiBatchArgs a;
   a.vtmp[0] = vtmp;
   a.count = 1; a.trans = trans; a.f32 = f32; a.eps = eps; a.dm1 = dm1; a.rmax = rmax;
   a.norm_in = norm_in; a.norm_out = norm_out; a.err = err_flag;
   a.G[0] = G; a.l[0] = l; a.GV[0] = GV; a.V[0] = V; a.sigma[0] = sigma; a.rank_out[0] = rank_out;
-  jacobi_svd_batched(a, st);
+  if (f32 || !pre) {
+    jacobi_svd_batched(a, st);
+    return;
+  }
+  // FP64 result in two passes: FP32 sweeps give rotations V32 (orthogonal to
+  // about single precision); two Newton-Schulz steps X <- X (3 I - X^T X) / 2
+  // in FP64 make them orthogonal to double rounding (each step squares the
+  // error); FP64 sweeps on op(G) V32 starting from V32 then only have the
+  // remaining rotations to do (the FP64 pipe is slow on this part)
+  double* V32 = pre;
+  double* A0 = pre + l * l;
+  double* Tm = pre + 2 * l * l;
+  double* Cn = pre + 3 * l * l;
+  JacobiBatchArgs p1 = a;
+  p1.f32 = 1;
+  p1.norm_in = nullptr;
+  p1.norm_out = nullptr;
+  p1.V[0] = V32;
+  jacobi_svd_batched(p1, st);
+  for (int it = 0; it < 2; ++it) {
+    GemmProblem t;  // Tm = X^T X
+    t.M = (int)l; t.N = (int)l; t.K = (int)l;
+    t.A = V32; t.sAm = 1; t.sAk = l;
+    t.B = V32; t.sBk = l; t.sBn = 1;
+    t.C = Tm; t.sCm = l; t.sCn = 1;
+    gemm(TT_MODE_FP64, {t}, st);
+    CopySeg cs;
+    cs.src = V32; cs.dst = Cn; cs.A = l * l; cs.sa = 1; cs.src_f64 = cs.dst_f64 = 1;
+    copy3d({cs}, st);
+    GemmProblem u = gemm_rm((int)l, (int)l, (int)l, V32, l, Tm, l, Cn, l, -0.5, 1.5);
+    gemm(TT_MODE_FP64, {u}, st);
+    std::swap(V32, Cn);
+  }
+  GemmProblem g;
+  g.M = (int)l; g.N = (int)l; g.K = (int)l;
+  g.A = G; g.sAm = trans ? 1 : l; g.sAk = trans ? l : 1;  // op(G)
+  g.B = V32; g.sBk = l; g.sBn = 1;
+  g.C = A0; g.sCm = l; g.sCn = 1;
+  gemm(TT_MODE_FP64, {g}, st);
+  JacobiBatchArgs p2 = a;
+  p2.trans = 0;
+  p2.G[0] = A0;
+  p2.v0[0] = V32;
+  jacobi_svd_batched(p2, st);
 }
 
 }  // namespace ttsg

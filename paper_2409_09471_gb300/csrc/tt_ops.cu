@@ -488,6 +488,7 @@ void tt_round_rand_dev(const Ctx& c, const std::vector<Term<T>>& terms, double e
   for (int k = 1; k < d; ++k) gws = std::max(gws, gram_workspace(n[k] * ell[k + 1], ell[k]));
   void* gw = f64 ? nullptr : ar.take<char>((int64_t)gws);
   double* Vs = ar.take<double>(lmax * lmax);  // Jacobi V scratch for large bonds
+  double* Pre = ar.take<double>(4 * lmax * lmax);  // FP32 pre-pass of the FP64 Jacobi
 
   const T* cur = H[d - 1];
   int64_t rr = 1;
@@ -502,7 +503,7 @@ void tt_round_rand_dev(const Ctx& c, const std::vector<Term<T>>& terms, double e
       gram_f64(cur, 0, cc, L, 1, cc, Gb, gw, gws, c.st);
       chol_f64(Gb, L, 1e-14, Rf, c.err + 2, c.st);
       jacobi_svd(Rf, L, 0, 1, GV, Vd, sig, eps, d - 1, rmax, mu == d ? nullptr : nrm,
-                 mu == d ? nrm : nullptr, rk, c.err + 1, c.st, Vs);
+                 mu == d ? nrm : nullptr, rk, c.err + 1, c.st, Vs, Pre);
       r = read_int(c, rk);
       if (!g_dry_run) {
         trunc_factors_kernel<T><<<(unsigned)std::max<int64_t>(1, std::min<int64_t>(
@@ -518,7 +519,7 @@ void tt_round_rand_dev(const Ctx& c, const std::vector<Term<T>>& terms, double e
       // X = cur (L x cc); X^T = Qt R  (Qt: cc x L)
       qr_f64(cur, f64, cc, L, 1, cc, Qt, f64, L, Rf, qw2, qws2, c.err, c.st);
       jacobi_svd(Rf, L, 1, f32svd, GV, Vd, sig, eps, d - 1, rmax, mu == d ? nullptr : nrm,
-                 mu == d ? nrm : nullptr, rk, c.err + 1, c.st, Vs);
+                 mu == d ? nrm : nullptr, rk, c.err + 1, c.st, Vs, Pre);
       r = read_int(c, rk);
       CopySeg s1, s2;
       s1.src = Vd; s1.dst = Vt; s1.A = L * L; s1.sa = 1; s1.src_f64 = 1; s1.dst_f64 = f64;
@@ -537,7 +538,7 @@ void tt_round_rand_dev(const Ctx& c, const std::vector<Term<T>>& terms, double e
       // X = Q2 R2 (Q2: L x cc), R2 V2 = U2 Sigma
       qr_f64(cur, f64, L, cc, cc, 1, Qt, f64, cc, Rf, qw2, qws2, c.err, c.st);
       jacobi_svd(Rf, cc, 0, f32svd, GV, Vd, sig, eps, d - 1, rmax, mu == d ? nullptr : nrm,
-                 mu == d ? nrm : nullptr, rk, c.err + 1, c.st, Vs);
+                 mu == d ? nrm : nullptr, rk, c.err + 1, c.st, Vs, Pre);
       r = read_int(c, rk);
       CopySeg s1, s2;
       s1.src = Vd; s1.dst = y.core[k]; s1.A = r; s1.B = cc; s1.sa = 1; s1.sb = cc;
