@@ -22,8 +22,12 @@
  *   TT_MODE_FP64  cores are double; every step in FP64.
  *   TT_MODE_FP32  cores are float; contractions in FP32 (CUDA cores),
  *                 Householder QR, least squares and residual checks in FP64.
- *   TT_MODE_TF32  cores are float; contractions on tcgen05 tensor cores in TF32
- *                 with FP32 accumulation; QR, least squares, residual in FP64.
+ *   TT_MODE_TF32  cores are float; the matvec core contractions (mode sizes a
+ *                 multiple of 4) on tcgen05 tensor cores in split TF32 (each
+ *                 operand as hi + lo TF32 parts, three products, FP32
+ *                 accumulation, about 2^-20 relative error per product);
+ *                 the other contractions as in TT_MODE_FP32; QR, least
+ *                 squares and residual checks in FP64.
  * Streams.  ``stream`` is a cudaStream_t (NULL = default stream).  Calls that
  *   return host values or data-dependent ranks synchronise that stream.
  * Workspace.  Entry points that need scratch take ``ws`` (device) and
