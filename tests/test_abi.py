@@ -84,3 +84,44 @@ def test_workspace_queries_run_without_a_gpu(built_lib):
         assert lib.tt_sketch_workspace(mode, ctypes.byref(x), 40) > 0
         arr = (_abi.TTVec * 2)(x, y)
         assert lib.tt_round_rand_workspace(mode, 2, arr, 8, 4) > 0
+
+
+def test_new_entry_points_reject_bad_arguments_on_the_host(built_lib):
+    from paper_2409_09471_gb300 import _abi
+    lib = _abi.lib
+    assert lib.tt_sgmres_solve_batched(None, 0, None, None, None, None, 4, None, 0) == 1
+    assert b"nrhs" in lib.tt_last_error()
+    assert lib.tt_qr_f64_batched(0, 0, None, None, None, None, None, None, 0, None) == 1
+    assert lib.tt_qr_f64_batched_workspace(0, None, None) == 0
+    assert lib.tt_dot_grad(0, None, None, None, None, 0, None) == 1
+    assert lib.tt_local_dots(0, None, None, None, None, None, 0, None) == 1
+    assert lib.tt_kron_sum_op(0, 0, None, None, None, None, None) == 1
+    assert lib.tt_op_transpose(0, None, None, None) == 1
+    assert lib.tt_kron_sum_op(7, 1, None, None, None, None, None) == 1  # unknown mode
+    assert b"mode" in lib.tt_last_error()
+
+
+def test_solver_workspace_queries_are_dry_runs(built_lib):
+    # the solver's workspace query runs the whole solve on the host with
+    # placeholder pointers and no CUDA work; the batched query is at least the
+    # per-worker slice times the workers
+    from paper_2409_09471_gb300 import _abi
+    lib = _abi.lib
+    d, ns = 4, [8, 8, 8, 8]
+    n = (ctypes.c_int64 * d)(*ns)
+    R = (ctypes.c_int64 * (d + 1))(1, 2, 2, 2, 1)
+    opc = (ctypes.c_void_p * d)(*([0x1000] * d))
+    op = _abi.TTOp(d, n, R, opc)
+    r = (ctypes.c_int64 * (d + 1))(1, 3, 4, 2, 1)
+    bc = (ctypes.c_void_p * d)(*([0x2000] * d))
+    b = _abi.TTVec(d, n, r, bc)
+    for mode in (0, 1, 2):
+        p = _abi.SolverParams(20, 40, 1e-6, 0.0, 0.1, 0.1, 16, 16, 4, 0, 2, mode)
+        one = lib.tt_sgmres_solve_workspace(ctypes.byref(op), ctypes.byref(b), ctypes.byref(p))
+        assert one > 0, lib.tt_last_error()
+        bs = (_abi.TTVec * 3)(b, b, b)
+        many = lib.tt_sgmres_solve_batched_workspace(ctypes.byref(op), 3, bs, ctypes.byref(p), 2)
+        assert many >= 2 * 256 and many > 0
+        # invalid parameters are rejected by the query itself
+        bad = _abi.SolverParams(0, 40, 1e-6, 0.0, 0.1, 0.1, 16, 16, 4, 0, 2, mode)
+        assert lib.tt_sgmres_solve_workspace(ctypes.byref(op), ctypes.byref(b), ctypes.byref(bad)) == 0
