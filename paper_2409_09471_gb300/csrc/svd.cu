@@ -8,6 +8,11 @@
 // alpha, beta: zeta = (beta - alpha) / (2 gamma),
 // t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)), c = 1/sqrt(1+t^2), s = c t.
 // A sweep without any rotation above the threshold l * eps ends the iteration.
+// Double-precision problems run in a cluster form (jacobi_cluster_kernel): the
+// pairs of a step are spread over up to 16 CTAs that pass the rotated columns
+// to each other through distributed shared memory.
+#include <cooperative_groups.h>
+
 #include "kernels.cuh"
 #include "prof.cuh"
 
@@ -250,7 +255,325 @@ jacobi_kernel(const __grid_constant__ JacobiBatch jb, int* err) {
   }
 }
 
+// ---------------------------------------------------------------- cluster form
+// The same sweeps with one problem spread over a cluster of CS CTAs: in every
+// parallel step, pair k is rotated by warp k / CS of CTA k % CS, which holds both
+// columns (of G V and of V, with their tracked squared norms) in its own shared
+// memory.  After the rotation each column is written straight into the shared
+// memory of the CTA that rotates it in the next step (double-buffered by step
+// parity), so one cluster barrier per step orders the whole exchange.  Every
+// CTA then does CS times less arithmetic per step; the FP64 pipe of one SM is
+// what bounds the one-CTA kernel in double precision.
+constexpr int JC_MAX_CS = 16;
+constexpr int JC_THREADS = 512;  // one warp per local pair
+
+// player held by slot (k, role) in round-robin step `step` (lp players)
+__device__ __forceinline__ int jc_col(int k, int role, int step, int lp) {
+  const int m = lp - 1;
+  if (k == 0) return role == 0 ? m : step;
+  int x = role == 0 ? step + k : step - k;
+  if (x >= m) x -= m;
+  if (x < 0) x += m;
+  return x;
+}
+// inverse: slot (k, role) of player x in step `step`
+__device__ __forceinline__ void jc_slot(int x, int step, int lp, int& k, int& role) {
+  const int m = lp - 1, npairs = lp >> 1;
+  if (x == m) { k = 0; role = 0; return; }
+  int d = x - step;
+  if (d < 0) d += m;
+  if (d == 0) { k = 0; role = 1; }
+  else if (d <= npairs - 1) { k = d; role = 0; }
+  else { k = m - d; role = 1; }
+}
+
+// Shared memory per CTA (ld = largest l of the launch, nplm = pairs per CTA):
+// A and V slots [2 buffers][nplm][2 roles][ld], norms [2][nplm][2], then the
+// gathered singular values (double[ld]) and the sweep flags (int[2][16]).
+__host__ __device__ inline size_t jc_smem_bytes(int ld, int nplm, size_t es) {
+  const size_t t = (8 * (size_t)nplm * ld + 4 * (size_t)nplm) * es;
+  return ((t + 7) & ~(size_t)7) + (size_t)ld * sizeof(double) + 2 * JC_MAX_CS * sizeof(int);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(JC_THREADS)
+jacobi_cluster_kernel(const __grid_constant__ JacobiBatch jb, int ld, int nplm, int* err) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cl = cg::this_cluster();
+  const int CS = (int)cl.num_blocks();
+  const int cr = (int)cl.block_rank();
+  const int bi = blockIdx.x / CS;
+  const double* G = jb.G[bi];
+  const int l = jb.l[bi], trans = jb.trans;
+  double* GV = jb.GV[bi];
+  double* V = jb.V[bi];
+  double* sigma = jb.sigma[bi];
+  const double* v0 = jb.v0[bi];
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  T* Ab = (T*)sm_raw;
+  T* Vb = Ab + (size_t)4 * nplm * ld;
+  T* Nb = Vb + (size_t)4 * nplm * ld;
+  double* nall = (double*)(sm_raw + (((8 * (size_t)nplm * ld + 4 * (size_t)nplm) * sizeof(T) + 7) &
+                                     ~(size_t)7));
+  int* flags = (int*)(nall + ld);
+  __shared__ int rotated;
+  __shared__ double s_tot;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int nthreads = blockDim.x;
+  const int lp = l + (l & 1), m = lp - 1, npairs = lp / 2;
+  const int kk = warp;              // local pair of this warp
+  const int k = kk * CS + cr;       // its pair index
+  const bool has_pair = kk < nplm && k < npairs;
+  auto slotA = [&](int b, int q, int role) { return Ab + ((size_t)(b * nplm + q) * 2 + role) * ld; };
+  auto slotV = [&](int b, int q, int role) { return Vb + ((size_t)(b * nplm + q) * 2 + role) * ld; };
+  auto slotN = [&](int b, int q, int role) { return Nb + (size_t)(b * nplm + q) * 2 + role; };
+
+  // ||G||_F^2 read by every CTA in the same order (identical thresholds)
+  if (warp == 0) {
+    double acc = 0.0;
+    for (int e = lane; e < l * l; e += 32) { const double x = (double)(T)G[e]; acc += x * x; }
+    acc = warp_sum_t(acc);
+    if (lane == 0) s_tot = acc;
+  }
+  // step-0 slots of this CTA's pairs
+  if (has_pair) {
+    for (int role = 0; role < 2; ++role) {
+      const int x = jc_col(k, role, 0, lp);
+      if (x >= l) continue;
+      T* a = slotA(0, kk, role);
+      T* v = slotV(0, kk, role);
+      for (int i = lane; i < l; i += 32) {
+        a[i] = (T)(trans ? G[(size_t)x * l + i] : G[(size_t)i * l + x]);
+        v[i] = v0 ? (T)v0[(size_t)i * l + x] : ((i == x) ? T(1) : T(0));
+      }
+    }
+  }
+  __syncthreads();
+  const T eps_t = sizeof(T) == 4 ? (T)1.1920929e-07 : (T)2.220446049250313e-16;
+  const T tol = (T)l * eps_t;
+  const T tot_t = (T)s_tot;
+  const T tiny = (T)(s_tot * (double)eps_t * (double)eps_t * (double)eps_t * (double)eps_t);
+  const T abs_thr = tol * eps_t * tot_t;
+  const T tol2 = tol * tol;
+  int buf = 0, sweep = 0;
+  for (; sweep < MAX_SWEEPS; ++sweep) {
+    // exact squared norms of the columns at the start of every sweep
+    if (has_pair) {
+      for (int role = 0; role < 2; ++role) {
+        if (jc_col(k, role, 0, lp) >= l) continue;
+        const T* a = slotA(buf, kk, role);
+        T acc = 0;
+        for (int i = lane; i < l; i += 32) acc = fma(a[i], a[i], acc);
+        acc = warp_sum_t(acc);
+        if (lane == 0) *slotN(buf, kk, role) = acc;
+      }
+    }
+    if (tid == 0) rotated = 0;
+    __syncthreads();
+    for (int step = 0; step < m; ++step) {
+      const int nstep = step + 1 == m ? 0 : step + 1;
+      if (has_pair) {
+        const int xa = jc_col(k, 0, step, lp), xb = jc_col(k, 1, step, lp);
+        const T* a0 = slotA(buf, kk, 0);
+        const T* a1 = slotA(buf, kk, 1);
+        const T* u0p = slotV(buf, kk, 0);
+        const T* u1p = slotV(buf, kk, 1);
+        T n0 = *slotN(buf, kk, 0), n1 = *slotN(buf, kk, 1);
+        // where each column goes for the next step
+        T *da0 = nullptr, *dv0 = nullptr, *dn0 = nullptr;
+        T *da1 = nullptr, *dv1 = nullptr, *dn1 = nullptr;
+        if (xa < l) {
+          int k2, r2;
+          jc_slot(xa, nstep, lp, k2, r2);
+          const int dst = k2 % CS, q2 = k2 / CS;
+          da0 = cl.map_shared_rank(slotA(buf ^ 1, q2, r2), dst);
+          dv0 = cl.map_shared_rank(slotV(buf ^ 1, q2, r2), dst);
+          dn0 = cl.map_shared_rank(slotN(buf ^ 1, q2, r2), dst);
+        }
+        if (xb < l) {
+          int k2, r2;
+          jc_slot(xb, nstep, lp, k2, r2);
+          const int dst = k2 % CS, q2 = k2 / CS;
+          da1 = cl.map_shared_rank(slotA(buf ^ 1, q2, r2), dst);
+          dv1 = cl.map_shared_rank(slotV(buf ^ 1, q2, r2), dst);
+          dn1 = cl.map_shared_rank(slotN(buf ^ 1, q2, r2), dst);
+        }
+        bool rot = false;
+        T c = 1, sg = 0;
+        if (xa < l && xb < l) {
+          // rotation of (p, q) = (lower, higher index), as in the one-CTA kernel
+          const bool sw = xa > xb;
+          T g0 = 0, g1 = 0;
+          int i = lane;
+          for (; i + 32 < l; i += 64) {
+            g0 = fma(a0[i], a1[i], g0);
+            g1 = fma(a0[i + 32], a1[i + 32], g1);
+          }
+          if (i < l) g0 = fma(a0[i], a1[i], g0);
+          const T ga = warp_sum_t(g0 + g1);
+          const T al = sw ? n1 : n0, be = sw ? n0 : n1;
+          // (double: the squared form of the relative test saves two dependent
+          // square roots; float keeps the square roots against overflow)
+          const bool rel_ok = sizeof(T) == 4 ? fabs(ga) <= tol * sqrt(al) * sqrt(be)
+                                             : ga * ga <= tol2 * al * be;
+          if (!(ga == T(0) || al <= tiny || be <= tiny || rel_ok || fabs(ga) <= abs_thr)) {
+            T t;
+            // for |zeta| > 1e4, t = 1 / (2 zeta) to a relative 1/(4 zeta^2),
+            // below single rounding (and zeta^2 would overflow a float first)
+            if (sizeof(T) == 4) {
+              const float zeta = __fdividef((float)(be - al), 2.0f * (float)ga);
+              t = fabsf(zeta) > 1e4f ? (T)__fdividef(0.5f, zeta)
+                                     : (T)__fdividef(zeta >= 0.f ? 1.f : -1.f,
+                                                     fabsf(zeta) + sqrtf(1.f + zeta * zeta));
+              c = (T)rsqrtf(1.f + (float)(t * t));
+            } else {
+              // the angle only needs single precision (it sets how much of
+              // gamma is removed); c = 1/sqrt(1+t^2), s = c t in double keep
+              // the rotation orthogonal to double rounding
+              const double zeta = (double)(be - al) / (2.0 * (double)ga);
+              const float zf = (float)zeta;
+              t = fabs(zeta) > 1e4 ? (T)(0.5 / zeta)
+                                   : (T)__fdividef(zf >= 0.f ? 1.f : -1.f,
+                                                   fabsf(zf) + sqrtf(1.f + zf * zf));
+              c = (T)rsqrt(1.0 + (double)t * (double)t);
+            }
+            const T s = c * t;
+            const T nal = al - t * ga, nbe = be + t * ga;
+            if (sw) { n1 = nal; n0 = nbe; } else { n0 = nal; n1 = nbe; }
+            // role form of p' = c p - s q, q' = s p + c q
+            sg = sw ? -s : s;
+            rot = true;
+          }
+        }
+        for (int i = lane; i < l; i += 32) {
+          const T x0 = a0[i], x1 = a1[i], w0 = u0p[i], w1 = u1p[i];
+          if (da0) {
+            da0[i] = rot ? c * x0 - sg * x1 : x0;
+            dv0[i] = rot ? c * w0 - sg * w1 : w0;
+          }
+          if (da1) {
+            da1[i] = rot ? sg * x0 + c * x1 : x1;
+            dv1[i] = rot ? sg * w0 + c * w1 : w1;
+          }
+        }
+        if (lane == 0) {
+          if (dn0) *dn0 = n0;
+          if (dn1) *dn1 = n1;
+          if (rot) rotated = 1;
+        }
+      }
+      if (step == m - 1) {
+        __syncthreads();
+        if (tid == 0) *cl.map_shared_rank(flags + (sweep & 1) * JC_MAX_CS + cr, 0) = rotated;
+      }
+      cl.sync();
+      buf ^= 1;
+    }
+    // every CTA reads the same flags: the decision is uniform over the cluster
+    int any = 0;
+    for (int r = 0; r < CS; ++r) any |= *cl.map_shared_rank(flags + (sweep & 1) * JC_MAX_CS + r, 0);
+    if (!any) break;
+  }
+  if (cr == 0 && tid == 0) {
+    if (sweep == MAX_SWEEPS) atomicAdd(err, 1);  // non-convergence counter
+    atomicMax(err + 2, sweep);
+    atomicAdd(err + 3, sweep);
+    atomicAdd(err + 4, 1);
+  }
+  // column norms gathered in CTA 0, then descending order (ties by index)
+  if (has_pair) {
+    for (int role = 0; role < 2; ++role) {
+      const int x = jc_col(k, role, 0, lp);
+      if (x >= l) continue;
+      const T* a = slotA(buf, kk, role);
+      double acc = 0.0;
+      for (int i = lane; i < l; i += 32) { const double y = (double)a[i]; acc += y * y; }
+      acc = warp_sum_t(acc);
+      if (lane == 0) *cl.map_shared_rank(nall + x, 0) = sqrt(acc);
+    }
+  }
+  cl.sync();
+  if (cr != 0)
+    for (int j = tid; j < l; j += nthreads) nall[j] = *cl.map_shared_rank(nall + j, 0);
+  __syncthreads();
+  if (has_pair) {
+    for (int role = 0; role < 2; ++role) {
+      const int x = jc_col(k, role, 0, lp);
+      if (x >= l) continue;
+      int rank = 0;
+      for (int i = 0; i < l; ++i)
+        if (nall[i] > nall[x] || (nall[i] == nall[x] && i < x)) ++rank;
+      const T* a = slotA(buf, kk, role);
+      const T* v = slotV(buf, kk, role);
+      for (int i = lane; i < l; i += 32) {
+        GV[(size_t)i * l + rank] = (double)a[i];
+        V[(size_t)i * l + rank] = (double)v[i];
+      }
+    }
+  }
+  if (cr == 0) {
+    for (int j = tid; j < l; j += nthreads) {
+      int rank = 0;
+      for (int i = 0; i < l; ++i)
+        if (nall[i] > nall[j] || (nall[i] == nall[j] && i < j)) ++rank;
+      sigma[rank] = nall[j];
+    }
+    __syncthreads();
+    if (tid == 0) {
+      double tot = 0.0;
+      for (int i = 0; i < l; ++i) tot += sigma[i] * sigma[i];
+      const double nrm = jb.norm_in ? *jb.norm_in : sqrt(tot);
+      if (bi == 0 && jb.norm_out) *jb.norm_out = nrm;
+      const double delta = jb.eps * nrm / sqrt((double)(jb.dm1 > 0 ? jb.dm1 : 1));
+      double tail = 0.0;
+      int r = l;
+      for (int i = l - 1; i >= 0; --i) {
+        tail += sigma[i] * sigma[i];
+        if (sqrt(tail) <= delta) r = i; else break;
+      }
+      if (r > jb.rmax) r = (int)jb.rmax;
+      if (r < 1) r = 1;
+      *jb.rank_out[bi] = r;
+    }
+  }
+  // CTA 0's shared memory stays in place until every CTA has read the norms
+  cl.sync();
+}
+
 }  // namespace
+
+// Cluster launch of jacobi_cluster_kernel; false when the launch configuration
+// is refused (the caller then uses the one-CTA kernel).
+template <typename T>
+static bool launch_jacobi_cluster(const JacobiBatch& jb, int count, int cs, int ld, int nplm,
+                                  size_t smem, int* err, cudaStream_t st) {
+  static const bool attr_set = [] {
+    TT_CUDA(cudaFuncSetAttribute(jacobi_cluster_kernel<T>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    TT_CUDA(cudaFuncSetAttribute(jacobi_cluster_kernel<T>,
+                                 cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+    return true;
+  }();
+  (void)attr_set;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(count * cs));
+  cfg.blockDim = dim3((unsigned)(nplm * 32));
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = (unsigned)cs;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  if (cudaLaunchKernelEx(&cfg, jacobi_cluster_kernel<T>, jb, ld, nplm, err) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return false;
+  }
+  check_launch("jacobi_cluster_kernel");
+  return true;
+}
 
 void jacobi_svd_batched(const JacobiBatchArgs& a, cudaStream_t st) {
   if (g_dry_run || a.count == 0) return;
@@ -267,6 +590,31 @@ void jacobi_svd_batched(const JacobiBatchArgs& a, cudaStream_t st) {
     lmax = std::max<int64_t>(lmax, a.l[i]);
   }
   const size_t es = a.f32 ? 4 : 8;
+  if (!a.f32) {
+    // cluster form for double precision, where one SM's FP64 pipe bounds the
+    // one-CTA kernel (GB300, l = 74: 4.4 ms -> 1.35 ms).  In single precision
+    // a step is bound by its dependent chain and the barrier, not by the
+    // arithmetic, and the cluster form measured slower (9 problems, l = 74:
+    // 874 us against 786 us), so floats keep the one-CTA kernel.
+    // 16 CTAs per problem for up to 4 problems, else 8; never more CTAs than
+    // column pairs.
+    const int npm = (int)((lmax + 1) / 2);
+    int cs = a.count > 4 ? 8 : 16;
+    while (cs > 1 && cs / 2 >= npm) cs /= 2;
+    int nplm = (int)ceil_div(npm, cs);
+    size_t jsm = jc_smem_bytes((int)lmax, nplm, es);
+    if (jsm > 200 * 1024 && cs < JC_MAX_CS) {
+      cs = JC_MAX_CS;
+      nplm = (int)ceil_div(npm, cs);
+      jsm = jc_smem_bytes((int)lmax, nplm, es);
+    }
+    if (jsm <= 200 * 1024 && nplm * 32 <= JC_THREADS) {
+      const int tok = prof_begin(PROF_SVD, st);
+      const bool ok = launch_jacobi_cluster<double>(jb, a.count, cs, (int)lmax, nplm, jsm, a.err, st);
+      prof_end(tok, st, 0.0, 3.0 * lmax * lmax * 8.0 * a.count);
+      if (ok) return;
+    }
+  }
   const size_t tail = (size_t)(lmax + 2) * es + (size_t)lmax * sizeof(double) + 16;
   size_t smem = 2 * (size_t)lmax * lmax * es + tail;
   if (smem > 220 * 1024) {
