@@ -24,8 +24,11 @@ Modules
 ``closed_forms`` closed-form eigenpairs of the 1-D model matrices and the
                 fast-diagonalisation dense solve of Kronecker sums.
 ``adjoint``     dense gradient of ``||x(theta, b) - x_t||^2`` on tiny grids.
+``stta``        streaming TT approximation: two-sided sketches with Gaussian
+                TT-DRMs (dense definition and partial contractions) and the
+                recovery of the approximant from them.
 
 Parity status: every function has at least one pin in ``tests/test_oracle_*``
 except where a docstring says "parity unpinned".
 """
-from . import tt, rounding, solvers, philox, closed_forms, adjoint  # noqa: F401
+from . import tt, rounding, solvers, philox, closed_forms, adjoint, stta  # noqa: F401
