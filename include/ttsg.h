@@ -333,6 +333,51 @@ size_t tt_sgmres_solve_batched_workspace(const tt_op* A, int nrhs, const tt_vec*
                                          const tt_solver_params* p, int nworkers);
 
 /*
+ * Streaming tensor-train approximation (STTA, Sec. 3.3): two-sided sketches of
+ * TT vectors with Gaussian TT-DRMs, linear in the tensor, from which an
+ * approximant of fixed ranks is recovered without the tensor itself.  With x's
+ * cores C_k [t_{k-1}][n_k][t_k] (paper's 1-based numbering), a right DRM X of
+ * ranks r_k (the target ranks) and a left DRM Y of ranks l_k:
+ *   Psi_k   = (Y_{<=k-1}^T kron I) x_{<=k} X_{>k}, shape [l_{k-1}][n_k][r_k],
+ *             k = 1..d,
+ *   Omega_k = Y_{<=k}^T x_{<=k} X_{>k}, l_k x r_k row-major, k = 1..d-1,
+ * where x_{<=k} is the unfolding of x with rows (i_1..i_k), Y_{<=k} and X_{>k}
+ * the left and right interface matrices of the DRMs,
+ * computed through the left and right partial contractions of x.
+ *
+ * tt_stta_sketch - psi[k] = coef * Psi_{k+1} (+ psi[k] if accumulate) and
+ * omega[k] = coef * Omega_{k+1} (+ omega[k] if accumulate), so the sketches of
+ * a sum sum_i a_i x_i build up one term at a time.
+ * x, X, Y: TT vectors with equal d and mode sizes, cores in the mode's
+ * precision (TT_MODE_TF32 contracts in FP32 on CUDA cores); X->rank gives r,
+ * Y->rank gives l.  psi: host array of d device pointers (double); omega: host
+ * array of d-1 device pointers (double); the caller owns all of them.
+ * Errors: TT_ERR_ARG for mismatched d or mode sizes, null pointers.
+ */
+int tt_stta_sketch(int mode, const tt_vec* x, double coef, int accumulate, const tt_vec* X,
+                   const tt_vec* Y, double* const* psi, double* const* omega, void* ws,
+                   size_t ws_bytes, void* stream);
+size_t tt_stta_sketch_workspace(int mode, const tt_vec* x, const tt_vec* X, const tt_vec* Y);
+
+/*
+ * tt_stta_recover - cores of the STTA approximant from the sketches (FP64):
+ * core 1 = Psi_1 and, for k = 2..d, the right unfolding of core k is
+ * Omega_{k-1}^+ Psi_k (r_{k-1} x n_k r_k).  The pseudo-inverse is formed from
+ * the FP64 Householder QR Omega = Q R and the FP64 Jacobi SVD R = U S V^T:
+ * Omega^+ Psi = V S^-2 (R V)^T Q^T Psi, singular values at or below
+ * rcond * s_max treated as zero (rcond <= 0 selects 1e-12).
+ * n[d], r[d+1], l[d+1]: host arrays (r_0 = r_d = l_0 = l_d = 1, l_k >= r_k).
+ * psi, omega: as written by tt_stta_sketch.  cores: host array of d device
+ * pointers (double, [r_{k-1}][n_k][r_k]), owned by the caller.
+ * Errors: TT_ERR_ARG for bad sizes (l_k < r_k) or null pointers.  A
+ * rank-deficient Omega is handled by the cutoff, not reported.
+ */
+int tt_stta_recover(int d, const int64_t* n, const int64_t* r, const int64_t* l,
+                    const double* const* psi, const double* const* omega, double rcond,
+                    double* const* cores, void* ws, size_t ws_bytes, void* stream);
+size_t tt_stta_recover_workspace(int d, const int64_t* n, const int64_t* r, const int64_t* l);
+
+/*
  * Measurement support (no counterpart in the method): tt_profile(mask) clears
  * the launch records and, for every class bit set in mask (1 CUDA-core GEMM,
  * 2 FP64 Householder QR, 4 Jacobi SVD, 8 least squares, 16 copies / generators,

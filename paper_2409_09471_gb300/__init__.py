@@ -30,7 +30,7 @@ __all__ = ["TT", "tt_matvec", "tt_sketch", "tt_dot", "tt_round_rand", "tt_gaussi
            "tt_lstsq_f64", "tt_sgmres_solve", "MODE_FP64", "MODE_FP32", "MODE_TF32", "TTError",
            "LIB_PATH", "mode_dtype", "op_to_device", "tt_dot_grad", "tt_local_dots",
            "tt_kron_sum_op", "tt_op_transpose", "solve_loss", "tt_qr_f64_batched",
-           "tt_sgmres_solve_batched"]
+           "tt_sgmres_solve_batched", "tt_stta_sketch", "tt_stta_recover"]
 
 
 def mode_dtype(mode: int) -> torch.dtype:
@@ -294,6 +294,67 @@ def tt_dot_grad(x: TT, y: TT, mode: int = MODE_FP64, stream=None) -> List[torch.
     check(lib.tt_dot_grad(mode, ctypes.byref(xd), ctypes.byref(yd), gp,
                           ctypes.c_void_p(ws.data_ptr()), ws.numel(), _stream(stream)))
     return g
+
+
+def tt_stta_sketch(x: TT, X: TT, Y: TT, mode: int = MODE_FP64, coef: float = 1.0,
+                   out=None, stream=None):
+    """Two-sided STTA sketches of ``x`` with right DRM ``X`` (target ranks) and
+    left DRM ``Y``: ``(psi, omega)``, float64 device tensors ``psi[k]``
+    ``[l_k, n_k, r_{k+1}]`` and ``omega[k]`` ``[l_{k+1}, r_{k+1}]``.  With
+    ``out = (psi, omega)`` the sketches are accumulated into those tensors
+    (``out += coef * sketch(x)``) and returned."""
+    _check_dtype(x.cores + X.cores + Y.cores, mode)
+    dev = x.cores[0].device
+    r, l = X.ranks, Y.ranks
+    if out is None:
+        psi = [torch.empty((l[k], x.ns[k], r[k + 1]), dtype=torch.float64, device=dev)
+               for k in range(x.d)]
+        omega = [torch.empty((l[k + 1], r[k + 1]), dtype=torch.float64, device=dev)
+                 for k in range(x.d - 1)]
+        acc = 0
+    else:
+        psi, omega = out
+        acc = 1
+    xd, k1 = x._desc()
+    Xd, k2 = X._desc()
+    Yd, k3 = Y._desc()
+    pp = (ctypes.c_void_p * x.d)(*[t.data_ptr() for t in psi])
+    op = (ctypes.c_void_p * max(1, x.d - 1))(*[t.data_ptr() for t in omega])
+    ws = _workspace(lib.tt_stta_sketch_workspace(mode, ctypes.byref(xd), ctypes.byref(Xd),
+                                                 ctypes.byref(Yd)), dev)
+    check(lib.tt_stta_sketch(mode, ctypes.byref(xd), float(coef), acc, ctypes.byref(Xd),
+                             ctypes.byref(Yd), pp, op, ctypes.c_void_p(ws.data_ptr()), ws.numel(),
+                             _stream(stream)))
+    return psi, omega
+
+
+def tt_stta_recover(psi: Sequence[torch.Tensor], omega: Sequence[torch.Tensor],
+                    rcond: float = 0.0, stream=None) -> TT:
+    """FP64 cores of the STTA approximant from the sketches: core 1 = psi[0]
+    and core k = pinv(omega[k-2]) psi[k-1] (right unfoldings), the
+    pseudo-inverse with relative cutoff ``rcond`` (0: 1e-12)."""
+    d = len(psi)
+    dev = psi[0].device
+    n = [p.shape[1] for p in psi]
+    l = [1] + [p.shape[0] for p in psi[1:]] + [1]
+    r = [1] + [p.shape[2] for p in psi[:-1]] + [1]
+    cores = [torch.empty((r[k], n[k], r[k + 1]), dtype=torch.float64, device=dev)
+             for k in range(d)]
+    n_a = (ctypes.c_int64 * d)(*n)
+    r_a = (ctypes.c_int64 * (d + 1))(*r)
+    l_a = (ctypes.c_int64 * (d + 1))(*l)
+    psi = [p.contiguous() for p in psi]
+    omega = [o.contiguous() for o in omega]
+    pp = (ctypes.c_void_p * d)(*[p.data_ptr() for p in psi])
+    op = (ctypes.c_void_p * max(1, d - 1))(*[o.data_ptr() for o in omega])
+    cp = (ctypes.c_void_p * d)(*[c.data_ptr() for c in cores])
+    need = lib.tt_stta_recover_workspace(d, n_a, r_a, l_a)
+    if need == 0:
+        raise TTError(1, lib.tt_last_error().decode())
+    ws = _workspace(need, dev)
+    check(lib.tt_stta_recover(d, n_a, r_a, l_a, pp, op, float(rcond), cp,
+                              ctypes.c_void_p(ws.data_ptr()), ws.numel(), _stream(stream)))
+    return TT(cores)
 
 
 def tt_local_dots(x: TT, y: TT, mats: Sequence[torch.Tensor], mode: int = MODE_FP64,

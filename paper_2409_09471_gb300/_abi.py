@@ -93,6 +93,12 @@ def _load():
         "tt_local_dots_workspace": (sz, [cint, P(TTVec), P(TTVec)]),
         "tt_kron_sum_op": (cint, [cint, cint, c_i64p, c_vpp, P(dbl), c_vpp, V]),
         "tt_op_transpose": (cint, [cint, P(TTOp), c_vpp, V]),
+        "tt_stta_sketch": (cint, [cint, P(TTVec), dbl, cint, P(TTVec), P(TTVec), c_vpp, c_vpp,
+                                  V, sz, V]),
+        "tt_stta_sketch_workspace": (sz, [cint, P(TTVec), P(TTVec), P(TTVec)]),
+        "tt_stta_recover": (cint, [cint, c_i64p, c_i64p, c_i64p, c_vpp, c_vpp, dbl, c_vpp, V, sz,
+                                   V]),
+        "tt_stta_recover_workspace": (sz, [cint, c_i64p, c_i64p, c_i64p]),
         "tt_profile": (cint, [cint]),
         "tt_profile_read": (cint, [cint, P(dbl), c_i64p, P(dbl), P(dbl)]),
         "tt_launch_count": (i64, []),

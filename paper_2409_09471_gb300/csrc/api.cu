@@ -374,6 +374,99 @@ int tt_round_rand(int mode, int nterms, const tt_vec* terms, const double* coef,
   });
 }
 
+namespace ttsg {
+namespace {
+template <typename T>
+void do_stta_sketch(int mode, const tt_vec* x, double coef, int accumulate, const tt_vec* X,
+                    const tt_vec* Y, double* const* psi, double* const* omega, void* ws,
+                    size_t bytes, void* stream, bool dry) {
+  TTv<T> xv = view<T>(x, "x");
+  TTv<T> Xv = view<T>(X, "X (right DRM)");
+  TTv<T> Yv = view<T>(Y, "Y (left DRM)");
+  if (Xv.d != xv.d || Yv.d != xv.d) throw Error(TT_ERR_ARG, "stta_sketch: d mismatch");
+  same_modes(Xv.n, xv.n, xv.d, "stta_sketch");
+  same_modes(Yv.n, xv.n, xv.d, "stta_sketch");
+  if (!dry) {
+    if (!psi || (xv.d > 1 && !omega)) throw Error(TT_ERR_ARG, "stta_sketch: null psi or omega");
+    for (int k = 0; k < xv.d; ++k)
+      if (!psi[k] || (k + 1 < xv.d && !omega[k]))
+        throw Error(TT_ERR_ARG, "stta_sketch: null sketch pointer");
+  }
+  Carved cv = carve(mode, ws, bytes, stream, dry);
+  fix_ctx(cv);
+  std::vector<double*> none(MAXD, nullptr);  // placeholders of a dry run
+  tt_stta_sketch_dev<T>(cv.ctx, xv, coef, accumulate, Xv, Yv, dry ? none.data() : psi,
+                        dry ? none.data() : omega);
+  if (dry) throw (size_t)cv.ar.peak;
+}
+
+void do_stta_recover(int d, const int64_t* n, const int64_t* r, const int64_t* l,
+                     const double* const* psi, const double* const* omega, double rcond,
+                     double* const* cores, void* ws, size_t bytes, void* stream, bool dry) {
+  if (d < 1 || d > MAXD) throw Error(TT_ERR_ARG, "stta_recover: d out of range");
+  if (!n || !r || !l) throw Error(TT_ERR_ARG, "stta_recover: null size array");
+  if (r[0] != 1 || r[d] != 1 || l[0] != 1 || l[d] != 1)
+    throw Error(TT_ERR_ARG, "stta_recover: boundary ranks must be 1");
+  for (int k = 0; k < d; ++k) {
+    if (n[k] < 1 || r[k + 1] < 1 || l[k + 1] < 1)
+      throw Error(TT_ERR_ARG, "stta_recover: n, ranks >= 1");
+    if (l[k] < r[k]) throw Error(TT_ERR_ARG, "stta_recover: l_k >= r_k required");
+  }
+  if (!dry) {
+    if (!psi || !cores || (d > 1 && !omega)) throw Error(TT_ERR_ARG, "stta_recover: null array");
+    for (int k = 0; k < d; ++k)
+      if (!psi[k] || !cores[k] || (k + 1 < d && !omega[k]))
+        throw Error(TT_ERR_ARG, "stta_recover: null pointer");
+  }
+  Carved cv = carve(TT_MODE_FP64, ws, bytes, stream, dry);
+  fix_ctx(cv);
+  reset_flags(cv);
+  std::vector<double*> none(MAXD, nullptr);  // placeholders of a dry run
+  tt_stta_recover_dev(cv.ctx, d, n, r, l, dry ? none.data() : psi, dry ? none.data() : omega,
+                      rcond > 0.0 ? rcond : 1e-12, dry ? none.data() : cores);
+  if (dry) throw (size_t)cv.ar.peak;
+}
+}  // namespace
+}  // namespace ttsg
+
+size_t tt_stta_sketch_workspace(int mode, const tt_vec* x, const tt_vec* X, const tt_vec* Y) {
+  return measure([&] {
+    check_mode(mode);
+    if (mode == TT_MODE_FP64)
+      do_stta_sketch<double>(mode, x, 1.0, 0, X, Y, nullptr, nullptr, nullptr, 0, nullptr, true);
+    else
+      do_stta_sketch<float>(mode, x, 1.0, 0, X, Y, nullptr, nullptr, nullptr, 0, nullptr, true);
+  });
+}
+
+int tt_stta_sketch(int mode, const tt_vec* x, double coef, int accumulate, const tt_vec* X,
+                   const tt_vec* Y, double* const* psi, double* const* omega, void* ws,
+                   size_t ws_bytes, void* stream) {
+  return guarded([&] {
+    check_mode(mode);
+    if (mode == TT_MODE_FP64)
+      do_stta_sketch<double>(mode, x, coef, accumulate, X, Y, psi, omega, ws, ws_bytes, stream,
+                             false);
+    else
+      do_stta_sketch<float>(mode, x, coef, accumulate, X, Y, psi, omega, ws, ws_bytes, stream,
+                            false);
+  });
+}
+
+size_t tt_stta_recover_workspace(int d, const int64_t* n, const int64_t* r, const int64_t* l) {
+  return measure([&] {
+    do_stta_recover(d, n, r, l, nullptr, nullptr, 0.0, nullptr, nullptr, 0, nullptr, true);
+  });
+}
+
+int tt_stta_recover(int d, const int64_t* n, const int64_t* r, const int64_t* l,
+                    const double* const* psi, const double* const* omega, double rcond,
+                    double* const* cores, void* ws, size_t ws_bytes, void* stream) {
+  return guarded([&] {
+    do_stta_recover(d, n, r, l, psi, omega, rcond, cores, ws, ws_bytes, stream, false);
+  });
+}
+
 int tt_gaussian(int mode, void* out, int64_t count, uint64_t seed, uint64_t stream_id, double std_,
                 void* stream) {
   return guarded([&] {

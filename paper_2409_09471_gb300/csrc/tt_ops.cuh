@@ -62,6 +62,17 @@ template <typename T>
 void tt_round_rand_dev(const Ctx& c, const std::vector<Term<T>>& terms, double eps, int64_t rmax,
                        int64_t oversample, const DRMSource<T>& drm, TTv<T>& y);
 
+// STTA sketches of x with right DRM X and left DRM Y, accumulated into FP64
+// psi[0..d-1] and omega[0..d-2] (see tt_stta_sketch), and the recovery of the
+// approximant's FP64 cores from them (see tt_stta_recover).
+template <typename T>
+void tt_stta_sketch_dev(const Ctx& c, const TTv<T>& x, double coef, int accumulate,
+                        const TTv<T>& X, const TTv<T>& Y, double* const* psi,
+                        double* const* omega);
+void tt_stta_recover_dev(const Ctx& c, int d, const int64_t* n, const int64_t* r,
+                         const int64_t* l, const double* const* psi, const double* const* omega,
+                         double rcond, double* const* cores);
+
 // Sketch ranks l_mu of the randomized rounding (see tt_round_rand).
 void rto_ranks(const std::vector<const int64_t*>& term_ranks, const int64_t* n, int d,
                int64_t rmax, int64_t oversample, int64_t* ells);

@@ -125,3 +125,37 @@ def test_solver_workspace_queries_are_dry_runs(built_lib):
         # invalid parameters are rejected by the query itself
         bad = _abi.SolverParams(0, 40, 1e-6, 0.0, 0.1, 0.1, 16, 16, 4, 0, 2, mode)
         assert lib.tt_sgmres_solve_workspace(ctypes.byref(op), ctypes.byref(b), ctypes.byref(bad)) == 0
+
+
+def test_stta_entry_points_validate_and_size_on_the_host(built_lib):
+    # workspace queries of the STTA entry points are host dry runs; the
+    # recovery rejects left ranks below the target ranks
+    from paper_2409_09471_gb300 import _abi
+    lib = _abi.lib
+    d, ns = 4, [7, 5, 8, 6]
+
+    def desc(ranks):
+        n = (ctypes.c_int64 * d)(*ns)
+        r = (ctypes.c_int64 * (d + 1))(*ranks)
+        p = (ctypes.c_void_p * d)(*([0x1000] * d))
+        return _abi.TTVec(d, n, r, p), (n, r, p)
+
+    x, kx = desc([1, 4, 9, 3, 1])
+    X, kX = desc([1, 3, 5, 2, 1])
+    Y, kY = desc([1, 6, 8, 4, 1])
+    for mode in (0, 1, 2):
+        assert lib.tt_stta_sketch_workspace(mode, ctypes.byref(x), ctypes.byref(X),
+                                            ctypes.byref(Y)) > 0, lib.tt_last_error()
+    Z, kZ = desc([1, 3, 5, 2, 1])
+    Z.n[1] = 6                       # mode sizes differ from x
+    assert lib.tt_stta_sketch_workspace(0, ctypes.byref(x), ctypes.byref(X), ctypes.byref(Z)) == 0
+    assert b"mode sizes" in lib.tt_last_error()
+    n = (ctypes.c_int64 * d)(*ns)
+    r = (ctypes.c_int64 * (d + 1))(1, 3, 5, 2, 1)
+    ok = (ctypes.c_int64 * (d + 1))(1, 6, 8, 4, 1)
+    short = (ctypes.c_int64 * (d + 1))(1, 6, 4, 4, 1)
+    assert lib.tt_stta_recover_workspace(d, n, r, ok) > 0, lib.tt_last_error()
+    assert lib.tt_stta_recover_workspace(d, n, r, short) == 0
+    assert b"l_k >= r_k" in lib.tt_last_error()
+    assert lib.tt_stta_recover(d, n, r, ok, None, None, 0.0, None, None, 0, None) == 1
+    assert lib.tt_stta_sketch(0, None, 1.0, 0, None, None, None, None, None, 0, None) == 1

@@ -1,0 +1,135 @@
+"""GPU parity of the STTA sketch and recovery (Section 3.3) against the oracle:
+sketches element by element at sizes spanning several 64-wide GEMM tiles with
+ragged tails, sketches of a sum accumulated term by term, recovered cores, the
+exact recovery of a TT whose ranks are the target ranks, the cutoff on a
+rank-deficient Omega, and d = 1, 2.
+
+Tolerances: FP64 sketches 1e-12 relative to the largest entry; float modes
+(FP32 contractions) 2e-5; recovered FP64 tensors 1e-9 relative."""
+import numpy as np
+import pytest
+import torch
+
+import ttinputs as ti
+from oracle import tt as ott, stta as ostta
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def g():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2409_09471_gb300 as g
+    return g
+
+
+def rel_max(a, b):
+    return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
+
+
+def dev(g, cores, mode):
+    return g.TT.from_numpy(cores, g.mode_dtype(mode))
+
+
+NS = [64, 33, 48, 20, 9]
+XR = [1, 70, 90, 65, 12, 1]        # the tensor's ranks
+RR = [1, 30, 40, 36, 8, 1]         # target ranks (right DRM)
+LR = [1, 45, 52, 50, 10, 1]        # left DRM ranks
+
+
+@pytest.mark.parametrize("mode", [0, 1, 2])
+def test_sketch_parity(g, mode):
+    x = ti.random_tt(NS, XR, seed=61)
+    X = ti.gaussian_drm(NS, RR, seed=62)
+    Y = ti.gaussian_drm(NS, LR, seed=63)
+    if mode != 0:   # compare against the oracle on the float-rounded inputs
+        x, X, Y = [[c.astype(np.float32).astype(np.float64) for c in t] for t in (x, X, Y)]
+    P_ref, O_ref = ostta.sketch(x, X, Y)
+    psi, omega = g.tt_stta_sketch(dev(g, x, mode), dev(g, X, mode), dev(g, Y, mode), mode=mode)
+    tol = 1e-12 if mode == 0 else 2e-5
+    assert len(psi) == 5 and len(omega) == 4
+    for a, b in zip(psi, P_ref):
+        assert tuple(a.shape) == b.shape
+        assert rel_max(a.cpu().numpy(), b) <= tol
+    for a, b in zip(omega, O_ref):
+        assert rel_max(a.cpu().numpy(), b) <= tol
+
+
+def test_sketch_of_a_sum_accumulates(g):
+    ns = NS[:4]
+    A = ti.random_tt(ns, [1, 20, 33, 7, 1], seed=64)
+    B = ti.random_tt(ns, [1, 9, 70, 15, 1], seed=65)
+    X = ti.gaussian_drm(ns, [1, 10, 12, 6, 1], seed=66)
+    Y = ti.gaussian_drm(ns, [1, 14, 17, 9, 1], seed=67)
+    P_ref, O_ref = ostta.sketch_sum([(0.75, A), (-1.5, B)], X, Y)
+    Xd, Yd = dev(g, X, 0), dev(g, Y, 0)
+    out = g.tt_stta_sketch(dev(g, A, 0), Xd, Yd, coef=0.75)
+    out = g.tt_stta_sketch(dev(g, B, 0), Xd, Yd, coef=-1.5, out=out)
+    for a, b in zip(out[0] + out[1], P_ref + O_ref):
+        assert rel_max(a.cpu().numpy(), b) <= 1e-12
+
+
+def test_recover_parity_and_exact_recovery(g):
+    # target ranks equal to the tensor's ranks: the recovery is exact, and the
+    # recovered cores equal the oracle's (Omega has full column rank)
+    ns = [40, 33, 27, 16]
+    ranks = [1, 12, 30, 9, 1]
+    x = ti.random_tt(ns, ranks, seed=68)
+    X = ti.gaussian_drm(ns, ranks, seed=69)
+    Y = ti.gaussian_drm(ns, [1, 17, 38, 13, 1], seed=70)
+    P, O = ostta.sketch(x, X, Y)
+    ref = ostta.recover(P, O)
+    psi = [torch.as_tensor(p, device="cuda") for p in P]
+    omega = [torch.as_tensor(o, device="cuda") for o in O]
+    y = g.tt_stta_recover(psi, omega)
+    assert y.ranks == ranks
+    for a, b in zip(y.numpy(), ref):
+        assert rel_max(a, b) <= 1e-9
+    diff = ott.norm(ott.left_orthogonalize(ott.add([(1.0, y.numpy()), (-1.0, x)])))
+    assert diff <= 1e-9 * ott.norm(x)
+
+
+def test_sketch_then_recover_on_device(g):
+    # the whole path on the device: sketch in FP64, recover, compare with x
+    ns = [24, 17, 30, 12, 20]
+    ranks = [1, 8, 15, 14, 6, 1]
+    x = ti.random_tt(ns, ranks, seed=71)
+    X = ti.gaussian_drm(ns, ranks, seed=72)
+    Y = ti.gaussian_drm(ns, [1] + [k + 5 for k in ranks[1:-1]] + [1], seed=73)
+    psi, omega = g.tt_stta_sketch(dev(g, x, 0), dev(g, X, 0), dev(g, Y, 0))
+    y = g.tt_stta_recover(psi, omega)
+    diff = ott.norm(ott.left_orthogonalize(ott.add([(1.0, y.numpy()), (-1.0, x)])))
+    assert diff <= 1e-9 * ott.norm(x)
+
+
+def test_rank_deficient_omega_uses_the_cutoff(g):
+    ns = [12, 15, 10]
+    x = ti.random_tt(ns, [1, 2, 3, 1], seed=74)
+    X = ti.gaussian_drm(ns, [1, 5, 6, 1], seed=75)
+    Y = ti.gaussian_drm(ns, [1, 8, 9, 1], seed=76)
+    psi, omega = g.tt_stta_sketch(dev(g, x, 0), dev(g, X, 0), dev(g, Y, 0))
+    y = g.tt_stta_recover(psi, omega, rcond=1e-10)
+    assert all(np.all(np.isfinite(c)) for c in y.numpy())
+    diff = ott.norm(ott.left_orthogonalize(ott.add([(1.0, y.numpy()), (-1.0, x)])))
+    assert diff <= 1e-7 * ott.norm(x)
+
+
+def test_d1_and_d2(g):
+    v = [np.random.default_rng(77).standard_normal((1, 13, 1))]
+    one = [np.ones((1, 13, 1))]
+    psi, omega = g.tt_stta_sketch(dev(g, v, 0), dev(g, one, 0), dev(g, one, 0))
+    assert omega == []
+    y = g.tt_stta_recover(psi, omega)
+    assert np.allclose(y.numpy()[0], v[0], atol=0)
+    # d = 2: generalized Nystrom of a 30 x 25 matrix at rank 6
+    T = np.random.default_rng(78).standard_normal((30, 25))
+    x = [T.reshape(1, 30, 25), np.eye(25).reshape(25, 25, 1)]
+    X = ti.gaussian_drm([30, 25], [1, 6, 1], seed=79)
+    Y = ti.gaussian_drm([30, 25], [1, 9, 1], seed=80)
+    psi, omega = g.tt_stta_sketch(dev(g, x, 0), dev(g, X, 0), dev(g, Y, 0))
+    y = g.tt_stta_recover(psi, omega)
+    Xm = X[1][:, :, 0].T
+    Ym = Y[0][0]
+    gn = (T @ Xm) @ np.linalg.pinv(Ym.T @ T @ Xm) @ (Ym.T @ T)
+    assert rel_max(ott.full(y.numpy()).reshape(30, 25), gn) <= 1e-10
