@@ -34,7 +34,8 @@ class SolverParams(ctypes.Structure):
                 ("round_tol", ctypes.c_double), ("eta", ctypes.c_double),
                 ("stop_safety", ctypes.c_double), ("rmax", ctypes.c_int64),
                 ("r_sol", ctypes.c_int64), ("oversample", ctypes.c_int64),
-                ("seed", ctypes.c_uint64), ("max_restarts", ctypes.c_int), ("mode", ctypes.c_int)]
+                ("seed", ctypes.c_uint64), ("max_restarts", ctypes.c_int), ("mode", ctypes.c_int),
+                ("final_stta", ctypes.c_int)]
 
 
 class SolverInfo(ctypes.Structure):

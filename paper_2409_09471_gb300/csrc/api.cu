@@ -622,8 +622,9 @@ SolveParams to_params(const tt_solver_params* p) {
   q.maxit = p->maxit; q.s = p->s; q.tol = p->tol; q.round_tol = p->round_tol; q.eta = p->eta;
   q.stop_safety = p->stop_safety; q.rmax = p->rmax; q.r_sol = p->r_sol;
   q.oversample = p->oversample; q.seed = p->seed; q.max_restarts = p->max_restarts;
+  q.final_stta = p->final_stta;
   if (q.maxit < 1 || q.tol <= 0 || q.rmax < 1 || q.oversample < 0 || q.max_restarts < 0 ||
-      q.eta < 0 || q.stop_safety <= 0)
+      q.eta < 0 || q.stop_safety <= 0 || (q.final_stta != 0 && q.final_stta != 1))
     throw Error(TT_ERR_ARG, "solve: invalid parameters");
   return q;
 }

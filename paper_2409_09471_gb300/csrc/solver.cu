@@ -203,6 +203,69 @@ SolveResult sgmres_solve(const Ctx& c0, const TTop<double>& A64in, const TTv<dou
     copy3d(segs, c.st);
   };
 
+  // ---- STTA (Sec. 3.3, Alg. 4): each cycle's correction from one-pass
+  // sketches of the basis vectors instead of a rounding of the stored basis.
+  // Target ranks r_sol and left ranks r_sol + 20 (the paper's oversampling),
+  // both capped by the mode-size products; Gaussian TT-DRMs from the Philox
+  // streams 4096 + k (right) and 6144 + k (left).
+  const bool use_stta = p.final_stta != 0;
+  int64_t rS[MAXD + 1], lS[MAXD + 1];
+  TTv<T> Xv, Yv;
+  std::vector<int64_t> psi_off(d, 0), om_off(d, 0);
+  int64_t ssz = 0;
+  double* skb = nullptr;   // sketches of V[0..maxit-1], ssz doubles each
+  double* comb = nullptr;  // their combination with y
+  TTv<double> es;          // recovered correction (FP64, ranks rS)
+  if (use_stta) {
+    rS[0] = rS[d] = lS[0] = lS[d] = 1;
+    double left = 1.0;
+    for (int k = 1; k < d; ++k) {
+      left *= (double)n[k - 1];
+      double right = 1.0;
+      for (int q = k; q < d; ++q) right *= (double)n[q];
+      rS[k] = (int64_t)std::min<double>((double)r_sol, std::min(left, right));
+      lS[k] = (int64_t)std::min<double>((double)(rS[k] + 20), left);
+    }
+    Xv.d = Yv.d = d;
+    for (int k = 0; k <= d; ++k) { Xv.r[k] = rS[k]; Yv.r[k] = lS[k]; }
+    for (int k = 0; k < d; ++k) {
+      Xv.n[k] = Yv.n[k] = n[k];
+      const int64_t cx = rS[k] * n[k] * rS[k + 1], cy = lS[k] * n[k] * lS[k + 1];
+      Xv.core[k] = ar.take<T>(cx);
+      Yv.core[k] = ar.take<T>(cy);
+      gaussian_fill(Xv.core[k], f64, cx, p.seed, 4096 + (uint64_t)k, 1.0 / std::sqrt((double)cx),
+                    c.st);
+      gaussian_fill(Yv.core[k], f64, cy, p.seed, 6144 + (uint64_t)k, 1.0 / std::sqrt((double)cy),
+                    c.st);
+    }
+    for (int k = 0; k < d; ++k) { psi_off[k] = ssz; ssz += lS[k] * n[k] * rS[k + 1]; }
+    for (int k = 0; k + 1 < d; ++k) { om_off[k] = ssz; ssz += lS[k + 1] * rS[k + 1]; }
+    skb = ar.take<double>(ssz * p.maxit);
+    comb = ar.take<double>(ssz);
+    es = alloc_tt<double>(ar, d, n, rS);
+  }
+  auto stta_sketch_basis = [&](int i) {
+    std::vector<double*> ps(d), os(d, nullptr);
+    for (int k = 0; k < d; ++k) ps[k] = skb + (int64_t)i * ssz + psi_off[k];
+    for (int k = 0; k + 1 < d; ++k) os[k] = skb + (int64_t)i * ssz + om_off[k];
+    tt_stta_sketch_dev<T>(c, V[i], 1.0, 0, Xv, Yv, ps.data(), os.data());
+  };
+  // x <- Round(x + Omega^+ Psi) in FP64, Psi and Omega combined with y
+  auto stta_update_x = [&](int kdone, double final_tol, bool have) {
+    stta_combine(skb, ssz, kdone, ydev, comb, c.st);
+    std::vector<const double*> ps(d), os(d, nullptr);
+    for (int k = 0; k < d; ++k) ps[k] = comb + psi_off[k];
+    for (int k = 0; k + 1 < d; ++k) os[k] = comb + om_off[k];
+    tt_stta_recover_dev(c64, d, n, rS, lS, ps.data(), os.data(), f64 ? 1e-12 : 1e-6, es.core);
+    for (int q = 0; q <= d; ++q) es.r[q] = rS[q];
+    std::vector<Term<double>> terms;
+    if (have) { terms.emplace_back(); terms.back().X = x; }
+    terms.emplace_back();
+    terms.back().X = es;
+    tt_round_rand_dev<double>(c64, terms, final_tol, r_sol, p.oversample, drm64, xn);
+    copy_tt(xn, x, nullptr, 0);
+  };
+
   if (g_dry_run) {
     // workspace query: run every scratch-using step once at capacity ranks
     for (auto& v : V) for (int q = 0; q <= d; ++q) v.r[q] = vcap[q];
@@ -223,6 +286,10 @@ SolveResult sgmres_solve(const Ctx& c0, const TTop<double>& A64in, const TTv<dou
     true_residual_norm<double>(c, A64, b, x);
     u2[0].X = b; u2[1].X = w64;
     tt_round_rand_dev<double>(c64, u2, 0.1, p.rmax, p.oversample, drm64, r64);
+    if (use_stta) {
+      stta_sketch_basis(0);
+      stta_update_x(p.maxit, 0.1, true);
+    }
     return res;
   }
   // ||b|| in FP64 by the Gram sweep
@@ -251,6 +318,7 @@ SolveResult sgmres_solve(const Ctx& c0, const TTop<double>& A64in, const TTv<dou
     int kdone = 0;
     double sres = 1.0;
     for (int k = 0; k < p.maxit; ++k) {
+      if (use_stta) stta_sketch_basis(k);
       // w = A v_k
       for (int q = 0; q <= d; ++q) w.r[q] = A64.R[q] * V[k].r[q];
       tt_matvec_dev<T>(c, A, V[k], w);
@@ -294,6 +362,10 @@ SolveResult sgmres_solve(const Ctx& c0, const TTop<double>& A64in, const TTv<dou
       const size_t nh = res.res_hist.size();
       if (kdone >= 20 && res.res_hist[nh - 1] > 0.9 * res.res_hist[nh - 11]) break;
     }
+    if (use_stta) {
+      stta_update_x(kdone, final_tol, have_x);
+      have_x = true;
+    } else {
     // e = Round(sum_i y_i v_i)
     {
       std::vector<Term<T>> terms(kdone);
@@ -315,6 +387,7 @@ SolveResult sgmres_solve(const Ctx& c0, const TTop<double>& A64in, const TTv<dou
       terms[1].X = e64;
       tt_round_rand_dev<double>(c64, terms, final_tol, r_sol, p.oversample, drm64, xn);
       copy_tt(xn, x, nullptr, 0);
+    }
     }
     res.cycles = cyc + 1;
     res.sketched_res = sres;

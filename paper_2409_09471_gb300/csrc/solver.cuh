@@ -16,6 +16,7 @@ struct SolveParams {
   int64_t oversample = 10;
   uint64_t seed = 0;
   int max_restarts = 5;
+  int final_stta = 0;
 };
 
 struct SolveResult {

@@ -55,7 +55,28 @@ __global__ void stta_pinv_scale_kernel(double* __restrict__ B, int64_t rows, int
   }
 }
 
+// out[e] = sum_{i < k} y[i] * S[i * ssz + e]: the sketch of sum_i y_i v_i from
+// the stored sketches of the v_i (coefficients on the device).
+__global__ void stta_combine_kernel(const double* __restrict__ S, int64_t ssz, int k,
+                                    const double* __restrict__ y, double* __restrict__ out) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < ssz;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    double acc = 0.0;
+    for (int i = 0; i < k; ++i) acc = fma(y[i], S[(int64_t)i * ssz + e], acc);
+    out[e] = acc;
+  }
+}
+
 }  // namespace
+
+void stta_combine(const double* S, int64_t ssz, int k, const double* y, double* out,
+                  cudaStream_t st) {
+  if (g_dry_run || ssz <= 0) return;
+  const int threads = 256;
+  const int blocks = (int)std::min<int64_t>(ceil_div(ssz, threads), 152 * 8);
+  stta_combine_kernel<<<blocks, threads, 0, st>>>(S, ssz, k, y, out);
+  check_launch("stta_combine_kernel");
+}
 
 template <typename T>
 void tt_stta_sketch_dev(const Ctx& c, const TTv<T>& x, double coef, int accumulate,

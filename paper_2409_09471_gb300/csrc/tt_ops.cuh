@@ -72,6 +72,9 @@ void tt_stta_sketch_dev(const Ctx& c, const TTv<T>& x, double coef, int accumula
 void tt_stta_recover_dev(const Ctx& c, int d, const int64_t* n, const int64_t* r,
                          const int64_t* l, const double* const* psi, const double* const* omega,
                          double rcond, double* const* cores);
+// out = sum_{i < k} y[i] S_i for k sketches stored ssz doubles apart (y on the device).
+void stta_combine(const double* S, int64_t ssz, int k, const double* y, double* out,
+                  cudaStream_t st);
 
 // Sketch ranks l_mu of the randomized rounding (see tt_round_rand).
 void rto_ranks(const std::vector<const int64_t*>& term_ranks, const int64_t* n, int d,

@@ -122,9 +122,16 @@ def test_solver_workspace_queries_are_dry_runs(built_lib):
         bs = (_abi.TTVec * 3)(b, b, b)
         many = lib.tt_sgmres_solve_batched_workspace(ctypes.byref(op), 3, bs, ctypes.byref(p), 2)
         assert many >= 2 * 256 and many > 0
+        # the STTA form of the correction adds the DRMs and the stored sketches
+        ps = _abi.SolverParams(20, 40, 1e-6, 0.0, 0.1, 0.1, 16, 16, 4, 0, 2, mode, 1)
+        st = lib.tt_sgmres_solve_workspace(ctypes.byref(op), ctypes.byref(b), ctypes.byref(ps))
+        assert st > one, lib.tt_last_error()
         # invalid parameters are rejected by the query itself
         bad = _abi.SolverParams(0, 40, 1e-6, 0.0, 0.1, 0.1, 16, 16, 4, 0, 2, mode)
         assert lib.tt_sgmres_solve_workspace(ctypes.byref(op), ctypes.byref(b), ctypes.byref(bad)) == 0
+        bad2 = _abi.SolverParams(20, 40, 1e-6, 0.0, 0.1, 0.1, 16, 16, 4, 0, 2, mode, 3)
+        assert lib.tt_sgmres_solve_workspace(ctypes.byref(op), ctypes.byref(b),
+                                             ctypes.byref(bad2)) == 0
 
 
 def test_stta_entry_points_validate_and_size_on_the_host(built_lib):

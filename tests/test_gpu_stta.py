@@ -2,7 +2,8 @@
 sketches element by element at sizes spanning several 64-wide GEMM tiles with
 ragged tails, sketches of a sum accumulated term by term, recovered cores, the
 exact recovery of a TT whose ranks are the target ranks, the cutoff on a
-rank-deficient Omega, and d = 1, 2.
+rank-deficient Omega, d = 1, 2, and the solver with its correction formed by
+STTA (checked by the oracle's exact residual).
 
 Tolerances: FP64 sketches 1e-12 relative to the largest entry; float modes
 (FP32 contractions) 2e-5; recovered FP64 tensors 1e-9 relative."""
@@ -133,3 +134,28 @@ def test_d1_and_d2(g):
     Ym = Y[0][0]
     gn = (T @ Xm) @ np.linalg.pinv(Ym.T @ T @ Xm) @ (Ym.T @ T)
     assert rel_max(ott.full(y.numpy()).reshape(30, 25), gn) <= 1e-10
+
+
+@pytest.mark.parametrize("mode", [0, 1, 2])
+def test_solve_with_stta_correction(g, mode):
+    # Algorithm 4 with each cycle's correction sum_i y_i v_i recovered by STTA
+    # from one-pass sketches of the basis vectors: it reaches the tolerance by
+    # the oracle's exact FP64 residual, and two solutions with relative
+    # residual <= tol differ by at most 2 kappa tol (kappa = 48.2 for this 4-D
+    # convection-diffusion operator with n = 12, by sparse SVD and inverse
+    # iteration; the test allows 100)
+    from oracle import solvers as osol
+    w = ti.workload("convdiff", d=4, n=12, maxit=40)
+    op = g.op_to_device(w.op)
+    b = g.TT.from_numpy(w.b)
+    kw = dict(maxit=40, tol=1e-6, rmax=64, mode=mode, s=80, stop_safety=0.01, r_sol=64,
+              oversample=10, max_restarts=10)
+    xs, info = g.tt_sgmres_solve(op, b, final_stta=True, **kw)
+    assert info["status"] == 0, info
+    r = osol.true_residual_norm(w.op, xs.numpy(), w.b) / ott.norm(w.b)
+    assert r <= 1e-6
+    assert abs(r - info["true_res"]) <= 1e-2 * r + 1e-14
+    xr, ir = g.tt_sgmres_solve(op, b, **kw)
+    assert ir["status"] == 0
+    diff = ott.norm(ott.left_orthogonalize(ott.add([(1.0, xs.numpy()), (-1.0, xr.numpy())])))
+    assert diff <= 2 * 100 * 1e-6 * ott.norm(xr.numpy())
