@@ -283,10 +283,12 @@ typedef struct {
   int max_restarts;   /* restart cycles after the first */
   int mode;           /* TT_MODE_* */
   int final_stta;     /* 1: each cycle's correction sum_i y_i v_i by STTA (Sec. 3.3,
-                         Alg. 4) from one-pass sketches of the basis vectors (target
-                         ranks r_sol, left ranks r_sol + 20, DRM streams 4096 + k and
-                         6144 + k), then rounded in FP64 with x; 0: randomized
-                         rounding of the stored basis (default) */
+                         Alg. 4) from one-pass FP64 sketches of the basis vectors
+                         (target ranks r_sol, left ranks r_sol + 20, DRM streams
+                         4096 + k and 6144 + k), then rounded in FP64 with x (meant
+                         for TT_MODE_FP64: in the float modes its refinement converged
+                         far more slowly than the default); 0: randomized rounding of
+                         the stored basis (default) */
 } tt_solver_params;
 
 typedef struct {

@@ -10,6 +10,7 @@
 //   v~ = Round(w - h v_k, round_tol, rmax)  ->  v_{k+1} = v~ / ||v~||
 //   y = argmin ||W y - S r0||, stop when ||W y - S r0|| <= inner_tol ||S r0||.
 #include "solver.cuh"
+#include <type_traits>
 #include <chrono>
 #include <cmath>
 #include <cstdio>
@@ -207,10 +208,14 @@ SolveResult sgmres_solve(const Ctx& c0, const TTop<double>& A64in, const TTv<dou
   // sketches of the basis vectors instead of a rounding of the stored basis.
   // Target ranks r_sol and left ranks r_sol + 20 (the paper's oversampling),
   // both capped by the mode-size products; Gaussian TT-DRMs from the Philox
-  // streams 4096 + k (right) and 6144 + k (left).
+  // streams 4096 + k (right) and 6144 + k (left).  The sketches are FP64 in
+  // every mode: combined with the Krylov coefficients (a non-orthogonal basis,
+  // so with cancellation) single-precision sketches left the correction too
+  // inexact for the refinement to converge (FP32 mode stalled near 7e-5).
   const bool use_stta = p.final_stta != 0;
   int64_t rS[MAXD + 1], lS[MAXD + 1];
-  TTv<T> Xv, Yv;
+  TTv<double> Xv, Yv;
+  TTv<double> vs64;        // FP64 copy of a basis vector in the float modes
   std::vector<int64_t> psi_off(d, 0), om_off(d, 0);
   int64_t ssz = 0;
   double* skb = nullptr;   // sketches of V[0..maxit-1], ssz doubles each
@@ -231,13 +236,14 @@ SolveResult sgmres_solve(const Ctx& c0, const TTop<double>& A64in, const TTv<dou
     for (int k = 0; k < d; ++k) {
       Xv.n[k] = Yv.n[k] = n[k];
       const int64_t cx = rS[k] * n[k] * rS[k + 1], cy = lS[k] * n[k] * lS[k + 1];
-      Xv.core[k] = ar.take<T>(cx);
-      Yv.core[k] = ar.take<T>(cy);
-      gaussian_fill(Xv.core[k], f64, cx, p.seed, 4096 + (uint64_t)k, 1.0 / std::sqrt((double)cx),
+      Xv.core[k] = ar.take<double>(cx);
+      Yv.core[k] = ar.take<double>(cy);
+      gaussian_fill(Xv.core[k], 1, cx, p.seed, 4096 + (uint64_t)k, 1.0 / std::sqrt((double)cx),
                     c.st);
-      gaussian_fill(Yv.core[k], f64, cy, p.seed, 6144 + (uint64_t)k, 1.0 / std::sqrt((double)cy),
+      gaussian_fill(Yv.core[k], 1, cy, p.seed, 6144 + (uint64_t)k, 1.0 / std::sqrt((double)cy),
                     c.st);
     }
+    if (!f64) vs64 = alloc_tt<double>(ar, d, n, vcap.data());
     for (int k = 0; k < d; ++k) { psi_off[k] = ssz; ssz += lS[k] * n[k] * rS[k + 1]; }
     for (int k = 0; k + 1 < d; ++k) { om_off[k] = ssz; ssz += lS[k + 1] * rS[k + 1]; }
     skb = ar.take<double>(ssz * p.maxit);
@@ -248,7 +254,12 @@ SolveResult sgmres_solve(const Ctx& c0, const TTop<double>& A64in, const TTv<dou
     std::vector<double*> ps(d), os(d, nullptr);
     for (int k = 0; k < d; ++k) ps[k] = skb + (int64_t)i * ssz + psi_off[k];
     for (int k = 0; k + 1 < d; ++k) os[k] = skb + (int64_t)i * ssz + om_off[k];
-    tt_stta_sketch_dev<T>(c, V[i], 1.0, 0, Xv, Yv, ps.data(), os.data());
+    if constexpr (std::is_same<T, double>::value) {
+      tt_stta_sketch_dev<double>(c64, V[i], 1.0, 0, Xv, Yv, ps.data(), os.data());
+    } else {
+      copy_tt(V[i], vs64, nullptr, 0);
+      tt_stta_sketch_dev<double>(c64, vs64, 1.0, 0, Xv, Yv, ps.data(), os.data());
+    }
   };
   // x <- Round(x + Omega^+ Psi) in FP64, Psi and Omega combined with y
   auto stta_update_x = [&](int kdone, double final_tol, bool have) {
@@ -256,7 +267,7 @@ SolveResult sgmres_solve(const Ctx& c0, const TTop<double>& A64in, const TTv<dou
     std::vector<const double*> ps(d), os(d, nullptr);
     for (int k = 0; k < d; ++k) ps[k] = comb + psi_off[k];
     for (int k = 0; k + 1 < d; ++k) os[k] = comb + om_off[k];
-    tt_stta_recover_dev(c64, d, n, rS, lS, ps.data(), os.data(), f64 ? 1e-12 : 1e-6, es.core);
+    tt_stta_recover_dev(c64, d, n, rS, lS, ps.data(), os.data(), 1e-12, es.core);
     for (int q = 0; q <= d; ++q) es.r[q] = rS[q];
     std::vector<Term<double>> terms;
     if (have) { terms.emplace_back(); terms.back().X = x; }
