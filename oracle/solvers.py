@@ -1,8 +1,9 @@
 """Krylov solvers in float64: sketched least squares, TT-sGMRES, TT-GMRES.
 
 ``tt_sgmres`` is the enhanced TT-sGMRES of Algorithm 4 with incomplete
-orthogonalisation parameter l = 1, carried out explicitly in TT format (the
-Remark after Section 3.6 recommends keeping the last vector for l = 1), with
+orthogonalisation against the last ``l`` basis vectors (default 1), carried
+out explicitly in TT format (the Remark after Section 3.6 recommends keeping
+the last vectors for small l), with
 randomize-then-orthogonalize rounding for the Gram-Schmidt step and for the
 final solution ``x = sum_i y_i v_i`` (Section 3.5), the operator applied
 without truncation (Section 3.2), and ``y_k = (S A V_k)^+ S r_0``
@@ -40,8 +41,8 @@ def true_residual_norm(op, x, b):
 
 
 def tt_sgmres(op, b, S, drm, maxit, tol, round_tol, rmax, oversample=10,
-              r_sol=None, final_tol=None):
-    """Algorithm 4 with l = 1, zero initial guess, RTO rounding.
+              r_sol=None, final_tol=None, ell=1):
+    """Algorithm 4, zero initial guess, RTO rounding.
 
     Parameters
     ----------
@@ -54,9 +55,13 @@ def tt_sgmres(op, b, S, drm, maxit, tol, round_tol, rmax, oversample=10,
     round_tol : relative tolerance of the Gram-Schmidt rounding (``eta tol``).
     rmax : rank cap of the basis vectors.
     r_sol, final_tol : rank cap and tolerance of the final rounding.
+    ell : incomplete orthogonalisation: ``h_{i,k} = w^T v_i`` for the last
+        ``ell`` basis vectors and ``v~ = Round(w - sum_i h_{i,k} v_i)``
+        (Section 3.5).
 
-    Returns ``(x, info)`` with the sketched residual history, basis ranks and
-    the number of iterations.
+    Returns ``(x, info)`` with the sketched residual history, basis ranks, the
+    number of iterations, the basis ``V`` and the coefficients ``H``
+    (``H[i][k] = h_{i,k}``, with ``h_{k+1,k}`` the norm of the rounded vector).
     """
     r_sol = rmax if r_sol is None else r_sol
     final_tol = round_tol if final_tol is None else final_tol
@@ -67,15 +72,20 @@ def tt_sgmres(op, b, S, drm, maxit, tol, round_tol, rmax, oversample=10,
     V = [v]
     Wcols = []
     hist, rank_hist = [], []
+    H = np.zeros((maxit + 1, maxit))
     y = None
     k = 0
     for k in range(1, maxit + 1):
         w = ttm.matvec(op, V[-1])                       # untruncated A v_k
         Wcols.append(ttm.sketch_kr_fast(w, S))          # W_k = [W_{k-1}, S w]
-        h = ttm.dot(w, V[-1])                            # h_{k,k} = w^T v_k
-        vt = rnd.rto_round([(1.0, w), (-h, V[-1])], drm, eps=round_tol, rmax=rmax,
-                           oversample=oversample)
+        first = max(0, len(V) - ell)
+        terms = [(1.0, w)]
+        for i in range(first, len(V)):                  # h_{i,k} = w^T v_i
+            H[i, k - 1] = ttm.dot(w, V[i])
+            terms.append((-H[i, k - 1], V[i]))
+        vt = rnd.rto_round(terms, drm, eps=round_tol, rmax=rmax, oversample=oversample)
         hn = ttm.norm(vt)                                # h_{k+1,k}
+        H[k, k - 1] = hn
         y, res = sketched_lstsq(np.stack(Wcols, axis=1), Sr0)
         hist.append(res / betaS)
         rank_hist.append(max(ttm.ranks(vt)))
@@ -84,11 +94,11 @@ def tt_sgmres(op, b, S, drm, maxit, tol, round_tol, rmax, oversample=10,
         V.append(ttm.scale(vt, 1.0 / hn))
     terms = [(float(y[i]), V[i]) for i in range(len(y))]
     x = rnd.rto_round(terms, drm, eps=final_tol, rmax=r_sol, oversample=oversample)
-    return x, dict(iters=k, res_hist=hist, rank_hist=rank_hist)
+    return x, dict(iters=k, res_hist=hist, rank_hist=rank_hist, V=V, H=H[:k + 1, :k])
 
 
 def solve(op, b, S, drm, maxit, tol, round_tol, rmax, oversample=10, r_sol=None,
-          final_tol=None, stop_safety=0.1, max_restarts=5, res_tol=None):
+          final_tol=None, stop_safety=0.1, max_restarts=5, res_tol=None, ell=1):
     """Restarted TT-sGMRES (Section 3.4): run :func:`tt_sgmres` on the current
     residual, update ``x <- Round(x + e)``, recompute the true residual
     ``r = b - A x`` exactly and stop when ``||r|| / ||b|| <= tol``.
@@ -109,7 +119,8 @@ def solve(op, b, S, drm, maxit, tol, round_tol, rmax, oversample=10, r_sol=None,
     for cyc in range(max_restarts + 1):
         inner_tol = min(0.5, stop_safety * tol / rel)
         e, info = tt_sgmres(op, rhs, S, drm, maxit, inner_tol, round_tol, rmax,
-                            oversample=oversample, r_sol=r_sol, final_tol=final_tol)
+                            oversample=oversample, r_sol=r_sol, final_tol=final_tol, ell=ell)
+        info = {k: v for k, v in info.items() if k not in ("V", "H")}
         total += info["iters"]
         if x is None:
             x = e

@@ -86,3 +86,41 @@ def test_true_residual_norm_exact():
     A = tt.op_full(w.op)
     expect = np.linalg.norm(tt.full(w.b) - A @ tt.full(x))
     assert np.isclose(solvers.true_residual_norm(w.op, x, w.b), expect, rtol=1e-12)
+
+
+def test_full_orthogonalisation_gives_arnoldi():
+    # l = maxit and no truncation (RTO at tolerance 0 with the rank cap above
+    # every representation rank is exact): the basis is orthonormal and
+    # A v_k = sum_{i <= k+1} h_{i,k} v_i holds (the Arnoldi relation of
+    # Section 3.5); with l = 1 the basis is not orthogonal
+    w = ti.workload("convdiff", d=3, n=5, rank=2)
+    ns = w.ns
+    S = philox.sketch_factors(ns, 20, 0)
+    drm = philox.drm_cores(ns, [1, 400, 400, 1], 1)
+    A = tt.op_full(w.op)
+    x, info = solvers.tt_sgmres(w.op, w.b, S, drm, 8, 1e-14, 0.0, 400, oversample=0, ell=8)
+    V = np.array([tt.full(v) for v in info["V"]])
+    k = info["iters"]
+    assert np.abs(V @ V.T - np.eye(len(V))).max() <= 1e-10
+    H = info["H"]
+    for j in range(min(k, len(V) - 1)):
+        lhs = A @ V[j]
+        rhs = sum(H[i, j] * V[i] for i in range(j + 2))
+        assert np.linalg.norm(lhs - rhs) <= 1e-10 * np.linalg.norm(lhs)
+    _, info1 = solvers.tt_sgmres(w.op, w.b, S, drm, 8, 1e-14, 0.0, 400, oversample=0, ell=1)
+    V1 = np.array([tt.full(v) for v in info1["V"]])
+    assert np.abs(V1 @ V1.T - np.eye(len(V1))).max() > 1e-3
+
+
+def test_partial_orthogonalisation_solves():
+    # l = 3 on the small convection-diffusion system: the restarted solve
+    # reaches the tolerance and matches the dense solution
+    w = ti.workload("convdiff", d=3, n=8)
+    p = w.params
+    S, drm = _setup(w)
+    x, info = solvers.solve(w.op, w.b, S, drm, 40, 1e-8, 1e-10, p["rmax"], p["oversample"],
+                            ell=3, stop_safety=0.01)
+    A = tt.op_full(w.op)
+    xd = np.linalg.solve(A, tt.full(w.b))
+    assert info["true_res"] <= 1e-8
+    assert np.linalg.norm(tt.full(x) - xd) / np.linalg.norm(xd) <= 1e-6
