@@ -289,6 +289,8 @@ typedef struct {
                          for TT_MODE_FP64: in the float modes its refinement converged
                          far more slowly than the default); 0: randomized rounding of
                          the stored basis (default) */
+  int ell;            /* incomplete orthogonalisation (Alg. 4, Sec. 3.5): v~ = Round(w -
+                         sum of h_{i,k} v_i over the last ell basis vectors); 0 => 1 */
 } tt_solver_params;
 
 typedef struct {

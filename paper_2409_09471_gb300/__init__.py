@@ -232,14 +232,16 @@ def tt_sgmres_solve(op, b: TT, maxit: int, tol: float, rmax: int, mode: int = MO
                     s: int = 0, round_tol: float = 0.0, eta: float = 0.1,
                     stop_safety: float = 0.1, r_sol: int = 0, oversample: int = 10, seed: int = 0,
                     max_restarts: int = 5, hist_cap: int = 1024, workspace=None, stream=None,
-                    raise_on_nonconvergence: bool = False, final_stta: bool = False):
+                    raise_on_nonconvergence: bool = False, final_stta: bool = False,
+                    ell: int = 1):
     """Restarted TT-sGMRES.  ``op`` and ``b`` in float64 on the device.
     Returns ``(x, info)``; ``x`` is a float64 :class:`TT`.  ``final_stta``
     forms each cycle's correction by STTA from one-pass sketches of the basis
-    vectors instead of rounding the stored basis."""
+    vectors instead of rounding the stored basis; ``ell`` orthogonalises each
+    new vector against the last ``ell`` basis vectors."""
     _check_dtype(list(op) + b.cores, MODE_FP64)
     p = SolverParams(maxit, s, tol, round_tol, eta, stop_safety, rmax, r_sol, oversample, seed,
-                     max_restarts, mode, int(bool(final_stta)))
+                     max_restarts, mode, int(bool(final_stta)), int(ell))
     od, k1 = _op_desc(op)
     bd, k2 = b._desc()
     dev = b.cores[0].device
@@ -500,13 +502,14 @@ def tt_sgmres_solve_batched(op, bs: Sequence[TT], maxit: int, tol: float, rmax: 
                             mode: int = MODE_FP64, s: int = 0, round_tol: float = 0.0,
                             eta: float = 0.1, stop_safety: float = 0.1, r_sol: int = 0,
                             oversample: int = 10, seed: int = 0, max_restarts: int = 5,
-                            nworkers: int = 16, workspace=None, final_stta: bool = False):
+                            nworkers: int = 16, workspace=None, final_stta: bool = False,
+                            ell: int = 1):
     """Independent solves ``A x_i = b_i`` for all right-hand sides (uneven ranks
     allowed) on ``nworkers`` library threads and streams.  Returns a list of
     ``(x_i, info_i)`` like :func:`tt_sgmres_solve`; synchronises."""
     _check_dtype(list(op) + [c for b in bs for c in b.cores], MODE_FP64)
     p = SolverParams(maxit, s, tol, round_tol, eta, stop_safety, rmax, r_sol, oversample, seed,
-                     max_restarts, mode, int(bool(final_stta)))
+                     max_restarts, mode, int(bool(final_stta)), int(ell))
     nrhs = len(bs)
     od, k1 = _op_desc(op)
     descs, keep = [], []

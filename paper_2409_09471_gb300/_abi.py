@@ -35,7 +35,7 @@ class SolverParams(ctypes.Structure):
                 ("stop_safety", ctypes.c_double), ("rmax", ctypes.c_int64),
                 ("r_sol", ctypes.c_int64), ("oversample", ctypes.c_int64),
                 ("seed", ctypes.c_uint64), ("max_restarts", ctypes.c_int), ("mode", ctypes.c_int),
-                ("final_stta", ctypes.c_int)]
+                ("final_stta", ctypes.c_int), ("ell", ctypes.c_int)]
 
 
 class SolverInfo(ctypes.Structure):

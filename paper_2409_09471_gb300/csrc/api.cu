@@ -623,6 +623,7 @@ SolveParams to_params(const tt_solver_params* p) {
   q.stop_safety = p->stop_safety; q.rmax = p->rmax; q.r_sol = p->r_sol;
   q.oversample = p->oversample; q.seed = p->seed; q.max_restarts = p->max_restarts;
   q.final_stta = p->final_stta;
+  q.ell = p->ell > 0 ? p->ell : 1;
   if (q.maxit < 1 || q.tol <= 0 || q.rmax < 1 || q.oversample < 0 || q.max_restarts < 0 ||
       q.eta < 0 || q.stop_safety <= 0 || (q.final_stta != 0 && q.final_stta != 1))
     throw Error(TT_ERR_ARG, "solve: invalid parameters");

@@ -171,6 +171,8 @@ SolveResult sgmres_solve(const Ctx& c0, const TTop<double>& A64in, const TTv<dou
   double* Wm = ar.take<double>(s * p.maxit);
   double* Sr0 = ar.take<double>(s);
   double* ydev = ar.take<double>(p.maxit);
+  const int ell = std::max(1, std::min(p.ell, p.maxit));
+  double* hcoef = ar.take<double>(p.maxit);  // h_{i,k} of the older vectors (ell > 1)
   double* scal = ar.take<double>(16);  // 0 beta, 1 h, 2 ||v~||^2, 3 ||v~||, 4 res, 5 ||Sr0||^2, 6 ||Sr0||
   double* lsws = (double*)ar.take<char>((int64_t)lstsq_workspace(s, p.maxit));
   if (f64) {
@@ -284,9 +286,10 @@ SolveResult sgmres_solve(const Ctx& c0, const TTop<double>& A64in, const TTv<dou
     tt_dot_dev<double>(Ctx{TT_MODE_FP64, c.st, c.ar, c.err, c.scratch}, b, b, scal + 8);
     tt_sketch_dev<T>(c, w, s, (const T* const*)S.data(), Wm);
     tt_dot_dev<T>(c, w, V[0], scal + 1);
-    std::vector<Term<T>> t2(2);
-    t2[0].X = w; t2[1].X = V[0];
-    tt_round_rand_dev<T>(c, t2, 0.1, p.rmax, p.oversample, drm, V[1]);
+    std::vector<Term<T>> t2(1 + ell);
+    t2[0].X = w;
+    for (int i = 0; i < ell; ++i) t2[1 + i].X = V[i];
+    tt_round_rand_dev<T>(c, t2, 0.1, p.rmax, p.oversample, drm, V[ell]);
     std::vector<Term<T>> tk(p.maxit);
     for (int i = 0; i < p.maxit; ++i) tk[i].X = V[i];
     tt_round_rand_dev<T>(c, tk, 0.1, r_sol, p.oversample, drm, e);
@@ -335,14 +338,19 @@ SolveResult sgmres_solve(const Ctx& c0, const TTop<double>& A64in, const TTv<dou
       tt_matvec_dev<T>(c, A, V[k], w);
       // W[:, k] = S w
       tt_sketch_dev<T>(c, w, s, (const T* const*)S.data(), Wm + k * s);
-      // h = <w, v_k>
-      tt_dot_dev<T>(c, w, V[k], scal + 1);
-      // v~ = Round(w - h v_k)
-      std::vector<Term<T>> terms(2);
+      // h_{i,k} = <w, v_i> for the last ell basis vectors (Sec. 3.5), then
+      // v~ = Round(w - sum_i h_{i,k} v_i)
+      const int first = std::max(0, k - ell + 1);
+      std::vector<Term<T>> terms(1 + (k - first + 1));
       terms[0].X = w;
-      terms[1].X = V[k];
-      terms[1].coef = -1.0;
-      terms[1].coef_dev = scal + 1;
+      for (int i = first; i <= k; ++i) {
+        double* hi = i == k ? scal + 1 : hcoef + i;
+        tt_dot_dev<T>(c, w, V[i], hi);
+        Term<T>& t = terms[1 + i - first];
+        t.X = V[i];
+        t.coef = -1.0;
+        t.coef_dev = hi;
+      }
       tt_round_rand_dev<T>(c, terms, round_tol, p.rmax, p.oversample, drm, V[k + 1]);
       // h_{k+1,k} = ||v~||: the norm of core 1 when cores 2..d are
       // right-orthogonal (FP64 mode), otherwise the Gram sweep

@@ -17,6 +17,7 @@ struct SolveParams {
   uint64_t seed = 0;
   int max_restarts = 5;
   int final_stta = 0;
+  int ell = 1;
 };
 
 struct SolveResult {

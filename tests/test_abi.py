@@ -126,6 +126,10 @@ def test_solver_workspace_queries_are_dry_runs(built_lib):
         ps = _abi.SolverParams(20, 40, 1e-6, 0.0, 0.1, 0.1, 16, 16, 4, 0, 2, mode, 1)
         st = lib.tt_sgmres_solve_workspace(ctypes.byref(op), ctypes.byref(b), ctypes.byref(ps))
         assert st > one, lib.tt_last_error()
+        # orthogonalising against 4 vectors rounds 5-term sums
+        pl = _abi.SolverParams(20, 40, 1e-6, 0.0, 0.1, 0.1, 16, 16, 4, 0, 2, mode, 0, 4)
+        four = lib.tt_sgmres_solve_workspace(ctypes.byref(op), ctypes.byref(b), ctypes.byref(pl))
+        assert four >= one, lib.tt_last_error()
         # invalid parameters are rejected by the query itself
         bad = _abi.SolverParams(0, 40, 1e-6, 0.0, 0.1, 0.1, 16, 16, 4, 0, 2, mode)
         assert lib.tt_sgmres_solve_workspace(ctypes.byref(op), ctypes.byref(b), ctypes.byref(bad)) == 0

@@ -90,3 +90,20 @@ def test_batch_of_one_converges_like_single_solve(g):
         assert r <= 1e-6
         assert abs(r - info["true_res"]) <= 1e-2 * r + 1e-14
     assert abs(ib["iters"] - is_["iters"]) <= 2
+
+
+@pytest.mark.parametrize("mode,ell", [(0, 3), (2, 2)])
+def test_partial_orthogonalisation(g, mode, ell):
+    # each new vector orthogonalised against the last ell basis vectors
+    # (Section 3.5): the restarted solve reaches the tolerance by the oracle's
+    # exact FP64 residual
+    w = ti.workload("convdiff", d=4, n=12, maxit=40)
+    op = g.op_to_device(w.op)
+    b = g.TT.from_numpy(w.b)
+    x, info = g.tt_sgmres_solve(op, b, maxit=40, tol=1e-6, rmax=64, mode=mode, s=80,
+                                stop_safety=0.01, r_sol=64, oversample=10, max_restarts=8,
+                                ell=ell)
+    assert info["status"] == 0, info
+    r = osol.true_residual_norm(w.op, x.numpy(), w.b) / ott.norm(w.b)
+    assert r <= 1e-6
+    assert abs(r - info["true_res"]) <= 1e-2 * r + 1e-14
