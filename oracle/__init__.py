@@ -27,8 +27,10 @@ Modules
 ``stta``        streaming TT approximation: two-sided sketches with Gaussian
                 TT-DRMs (dense definition and partial contractions) and the
                 recovery of the approximant from them.
+``precond``     exponential-sum right preconditioning of Kronecker-sum
+                operators and TT-sPGMRES (Algorithm 5).
 
 Parity status: every function has at least one pin in ``tests/test_oracle_*``
 except where a docstring says "parity unpinned".
 """
-from . import tt, rounding, solvers, philox, closed_forms, adjoint, stta  # noqa: F401
+from . import tt, rounding, solvers, philox, closed_forms, adjoint, stta, precond  # noqa: F401
