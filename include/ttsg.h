@@ -387,6 +387,58 @@ int tt_stta_recover(int d, const int64_t* n, const int64_t* r, const int64_t* l,
 size_t tt_stta_recover_workspace(int d, const int64_t* n, const int64_t* r, const int64_t* l);
 
 /*
+ * Exponential-sum right preconditioning (Sec. 3.7, Alg. 5) of an operator whose
+ * dominant part is a Kronecker sum A_0 = sum_k (I x .. x A_k x .. x I):
+ *   P^{-1} = sum_i alpha_i (exp(-beta_i A_1) x .. x exp(-beta_i A_d)) ~ A_0^{-1}.
+ * zeta: number of terms (1..256); alpha, beta: host arrays [zeta]; A1d: host
+ * array of d device pointers to the n_k x n_k row-major FP64 matrices A_k.
+ */
+typedef struct {
+  int zeta;
+  const double* alpha;
+  const double* beta;
+  const double* const* A1d;
+} tt_precond;
+
+/*
+ * tt_exp_sum_coefficients - alpha, beta with |z E(z) - 1| <~ tol on [a, b]
+ * (0 < a < b, 0 < tol < 1): the trapezoidal rule on 1/z = int exp(t - e^t z) dt
+ * (Trefethen-Weideman 2014) with step pi^2 / (2 log(1/tol)).  Returns the
+ * number of terms; alpha, beta (host, cap entries) are written only when it is
+ * <= cap.  Returns -1 for invalid arguments.  Host only.
+ */
+int tt_exp_sum_coefficients(double a, double b, double tol, int cap, double* alpha,
+                            double* beta);
+
+/*
+ * tt_precond_apply - y = Round(P^{-1} x): every core of x multiplied along its
+ * mode index by exp(-beta_i A_k) (FP64 Taylor of degree 18 with scaling and
+ * squaring, then the mode's precision), and the zeta-term sum rounded by the
+ * randomized rounding of tt_round_rand (DRM from the Philox stream seed,
+ * streams 2048 + k) to tolerance eps and ranks <= rmax.  y: output with
+ * capacities >= min(rmax, sketch ranks); ranks written to y->rank.
+ * Synchronises (reads the A_k to size the scaling).
+ */
+int tt_precond_apply(int mode, const tt_precond* P, const tt_vec* x, double eps, int64_t rmax,
+                     int64_t oversample, uint64_t seed, const tt_vec_out* y, void* ws,
+                     size_t ws_bytes, void* stream);
+size_t tt_precond_apply_workspace(int mode, const tt_precond* P, const tt_vec* x, int64_t rmax,
+                                  int64_t oversample);
+
+/*
+ * tt_spgmres_solve - right-preconditioned TT-sGMRES (TT-sPGMRES, Alg. 5): as
+ * tt_sgmres_solve, with w = A P^{-1} v_k (P^{-1} v_k rounded to rmax, the
+ * bounded-rank rounding of Sec. 3.8) and each cycle's correction
+ * P^{-1} Round(sum_i y_i v_i) rounded to r_sol.  The true residual is that of
+ * A x = b.  p->final_stta must be 0.
+ */
+int tt_spgmres_solve(const tt_op* A, const tt_precond* P, const tt_vec* b,
+                     const tt_solver_params* p, const tt_vec_out* x, tt_solver_info* info,
+                     void* ws, size_t ws_bytes, void* stream);
+size_t tt_spgmres_solve_workspace(const tt_op* A, const tt_precond* P, const tt_vec* b,
+                                  const tt_solver_params* p);
+
+/*
  * Measurement support (no counterpart in the method): tt_profile(mask) clears
  * the launch records and, for every class bit set in mask (1 CUDA-core GEMM,
  * 2 FP64 Householder QR, 4 Jacobi SVD, 8 least squares, 16 copies / generators,

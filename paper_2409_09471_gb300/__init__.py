@@ -21,16 +21,18 @@ import ctypes
 import os
 from typing import List, Sequence
 
+import numpy as np
 import torch
 
-from ._abi import (lib, TTVec, TTVecOut, TTOp, SolverParams, SolverInfo, MODE_FP64, MODE_FP32,
-                   MODE_TF32, TTError, check, LIB_PATH)
+from ._abi import (lib, TTVec, TTVecOut, TTOp, TTPrecond, SolverParams, SolverInfo, MODE_FP64,
+                   MODE_FP32, MODE_TF32, TTError, check, LIB_PATH)
 
 __all__ = ["TT", "tt_matvec", "tt_sketch", "tt_dot", "tt_round_rand", "tt_gaussian", "tt_qr_f64",
            "tt_lstsq_f64", "tt_sgmres_solve", "MODE_FP64", "MODE_FP32", "MODE_TF32", "TTError",
            "LIB_PATH", "mode_dtype", "op_to_device", "tt_dot_grad", "tt_local_dots",
            "tt_kron_sum_op", "tt_op_transpose", "solve_loss", "tt_qr_f64_batched",
-           "tt_sgmres_solve_batched", "tt_stta_sketch", "tt_stta_recover"]
+           "tt_sgmres_solve_batched", "tt_stta_sketch", "tt_stta_recover", "Precond",
+           "exp_sum_coefficients", "tt_precond_apply", "tt_spgmres_solve"]
 
 
 def mode_dtype(mode: int) -> torch.dtype:
@@ -233,19 +235,25 @@ def tt_sgmres_solve(op, b: TT, maxit: int, tol: float, rmax: int, mode: int = MO
                     stop_safety: float = 0.1, r_sol: int = 0, oversample: int = 10, seed: int = 0,
                     max_restarts: int = 5, hist_cap: int = 1024, workspace=None, stream=None,
                     raise_on_nonconvergence: bool = False, final_stta: bool = False,
-                    ell: int = 1):
+                    ell: int = 1, precond=None):
     """Restarted TT-sGMRES.  ``op`` and ``b`` in float64 on the device.
     Returns ``(x, info)``; ``x`` is a float64 :class:`TT`.  ``final_stta``
     forms each cycle's correction by STTA from one-pass sketches of the basis
     vectors instead of rounding the stored basis; ``ell`` orthogonalises each
-    new vector against the last ``ell`` basis vectors."""
+    new vector against the last ``ell`` basis vectors; ``precond`` (a
+    :class:`Precond`) selects right preconditioning (TT-sPGMRES)."""
     _check_dtype(list(op) + b.cores, MODE_FP64)
     p = SolverParams(maxit, s, tol, round_tol, eta, stop_safety, rmax, r_sol, oversample, seed,
                      max_restarts, mode, int(bool(final_stta)), int(ell))
     od, k1 = _op_desc(op)
     bd, k2 = b._desc()
     dev = b.cores[0].device
-    need = lib.tt_sgmres_solve_workspace(ctypes.byref(od), ctypes.byref(bd), ctypes.byref(p))
+    if precond is not None:
+        pdesc, k3 = precond._desc()
+        need = lib.tt_spgmres_solve_workspace(ctypes.byref(od), ctypes.byref(pdesc),
+                                              ctypes.byref(bd), ctypes.byref(p))
+    else:
+        need = lib.tt_sgmres_solve_workspace(ctypes.byref(od), ctypes.byref(bd), ctypes.byref(p))
     if need == 0:
         raise TTError(1, lib.tt_last_error().decode())
     if workspace is None or workspace.numel() < need:
@@ -266,10 +274,16 @@ def tt_sgmres_solve(op, b: TT, maxit: int, tol: float, rmax: int, mode: int = MO
     info.res_hist = ctypes.cast(rh, ctypes.POINTER(ctypes.c_double))
     info.rank_hist = ctypes.cast(kh, ctypes.POINTER(ctypes.c_int64))
     info.hist_cap = hist_cap
-    rc = lib.tt_sgmres_solve(ctypes.byref(od), ctypes.byref(bd), ctypes.byref(p),
-                             ctypes.byref(xd), ctypes.byref(info),
-                             ctypes.c_void_p(workspace.data_ptr()), workspace.numel(),
-                             _stream(stream))
+    if precond is not None:
+        rc = lib.tt_spgmres_solve(ctypes.byref(od), ctypes.byref(pdesc), ctypes.byref(bd),
+                                  ctypes.byref(p), ctypes.byref(xd), ctypes.byref(info),
+                                  ctypes.c_void_p(workspace.data_ptr()), workspace.numel(),
+                                  _stream(stream))
+    else:
+        rc = lib.tt_sgmres_solve(ctypes.byref(od), ctypes.byref(bd), ctypes.byref(p),
+                                 ctypes.byref(xd), ctypes.byref(info),
+                                 ctypes.c_void_p(workspace.data_ptr()), workspace.numel(),
+                                 _stream(stream))
     if rc not in (0, 5) or (rc == 5 and raise_on_nonconvergence):
         check(rc)
     r = list(rank_arr)
@@ -298,6 +312,79 @@ def tt_dot_grad(x: TT, y: TT, mode: int = MODE_FP64, stream=None) -> List[torch.
     check(lib.tt_dot_grad(mode, ctypes.byref(xd), ctypes.byref(yd), gp,
                           ctypes.c_void_p(ws.data_ptr()), ws.numel(), _stream(stream)))
     return g
+
+
+class Precond:
+    """Exponential-sum right preconditioner ``sum_i alpha_i (exp(-beta_i A_1) x
+    .. x exp(-beta_i A_d))`` of a Kronecker-sum operator: host coefficients and
+    the 1-D matrices ``A_k`` as float64 device tensors."""
+
+    def __init__(self, alpha, beta, mats: Sequence[torch.Tensor]):
+        self.alpha = np.ascontiguousarray(alpha, dtype=np.float64)
+        self.beta = np.ascontiguousarray(beta, dtype=np.float64)
+        if self.alpha.shape != self.beta.shape or self.alpha.ndim != 1:
+            raise ValueError("alpha and beta: equal-length vectors")
+        self.mats = [torch.as_tensor(m, dtype=torch.float64, device="cuda").contiguous()
+                     if not isinstance(m, torch.Tensor) else m.to(torch.float64).contiguous()
+                     for m in mats]
+
+    @classmethod
+    def for_interval(cls, a: float, b: float, tol: float, mats):
+        """Coefficients for the spectral interval [a, b] at accuracy tol."""
+        alpha, beta = exp_sum_coefficients(a, b, tol)
+        return cls(alpha, beta, mats)
+
+    def _desc(self):
+        ap = self.alpha.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        bp = self.beta.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        mp = (ctypes.c_void_p * len(self.mats))(*[m.data_ptr() for m in self.mats])
+        return TTPrecond(len(self.alpha), ap, bp, mp), (ap, bp, mp)
+
+
+def exp_sum_coefficients(a: float, b: float, tol: float):
+    """``(alpha, beta)`` of the exponential sum ``E(z) ~ 1/z`` on ``[a, b]``
+    (trapezoidal rule on the Laplace integral; host computation)."""
+    count = lib.tt_exp_sum_coefficients(float(a), float(b), float(tol), 0, None, None)
+    if count < 0:
+        raise TTError(1, "exp_sum_coefficients: need 0 < a < b and 0 < tol < 1")
+    alpha = np.zeros(count)
+    beta = np.zeros(count)
+    lib.tt_exp_sum_coefficients(float(a), float(b), float(tol), count,
+                                alpha.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                beta.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    return alpha, beta
+
+
+def tt_precond_apply(P: Precond, x: TT, eps: float, rmax: int, oversample: int = 10,
+                     seed: int = 0, mode: int = MODE_FP64, stream=None) -> TT:
+    """``Round(P^{-1} x)`` to ``eps`` and ranks ``<= rmax``."""
+    _check_dtype(x.cores, mode)
+    d, ns, dev, dt = x.d, x.ns, x.cores[0].device, x.cores[0].dtype
+    cap = [1] + [int(rmax)] * (d - 1) + [1]
+    ycores = [torch.empty(cap[k] * ns[k] * cap[k + 1], dtype=dt, device=dev) for k in range(d)]
+    n_arr = (ctypes.c_int64 * d)(*ns)
+    cap_arr = (ctypes.c_int64 * (d + 1))(*cap)
+    rank_arr = (ctypes.c_int64 * (d + 1))()
+    yptr = (ctypes.c_void_p * d)(*[c.data_ptr() for c in ycores])
+    yd = TTVecOut(d, n_arr, cap_arr, rank_arr, yptr)
+    xd, k1 = x._desc()
+    pd, k2 = P._desc()
+    need = lib.tt_precond_apply_workspace(mode, ctypes.byref(pd), ctypes.byref(xd), int(rmax),
+                                          int(oversample))
+    if need == 0:
+        raise TTError(1, lib.tt_last_error().decode())
+    ws = _workspace(need, dev)
+    check(lib.tt_precond_apply(mode, ctypes.byref(pd), ctypes.byref(xd), float(eps), int(rmax),
+                               int(oversample), ctypes.c_uint64(seed), ctypes.byref(yd),
+                               ctypes.c_void_p(ws.data_ptr()), ws.numel(), _stream(stream)))
+    r = list(rank_arr)
+    return TT([ycores[k][: r[k] * ns[k] * r[k + 1]].view(r[k], ns[k], r[k + 1]) for k in range(d)])
+
+
+def tt_spgmres_solve(op, P: Precond, b: TT, maxit: int, tol: float, rmax: int, **kw):
+    """Right-preconditioned TT-sGMRES (Algorithm 5); arguments as
+    :func:`tt_sgmres_solve`."""
+    return tt_sgmres_solve(op, b, maxit, tol, rmax, precond=P, **kw)
 
 
 def tt_stta_sketch(x: TT, X: TT, Y: TT, mode: int = MODE_FP64, coef: float = 1.0,

@@ -29,6 +29,11 @@ class TTOp(ctypes.Structure):
     _fields_ = [("d", ctypes.c_int), ("n", c_i64p), ("rank", c_i64p), ("core", c_vpp)]
 
 
+class TTPrecond(ctypes.Structure):
+    _fields_ = [("zeta", ctypes.c_int), ("alpha", ctypes.POINTER(ctypes.c_double)),
+                ("beta", ctypes.POINTER(ctypes.c_double)), ("A1d", c_vpp)]
+
+
 class SolverParams(ctypes.Structure):
     _fields_ = [("maxit", ctypes.c_int), ("s", ctypes.c_int), ("tol", ctypes.c_double),
                 ("round_tol", ctypes.c_double), ("eta", ctypes.c_double),
@@ -100,6 +105,13 @@ def _load():
         "tt_stta_recover": (cint, [cint, c_i64p, c_i64p, c_i64p, c_vpp, c_vpp, dbl, c_vpp, V, sz,
                                    V]),
         "tt_stta_recover_workspace": (sz, [cint, c_i64p, c_i64p, c_i64p]),
+        "tt_exp_sum_coefficients": (cint, [dbl, dbl, dbl, cint, P(dbl), P(dbl)]),
+        "tt_precond_apply": (cint, [cint, P(TTPrecond), P(TTVec), dbl, i64, i64, u64,
+                                    P(TTVecOut), V, sz, V]),
+        "tt_precond_apply_workspace": (sz, [cint, P(TTPrecond), P(TTVec), i64, i64]),
+        "tt_spgmres_solve": (cint, [P(TTOp), P(TTPrecond), P(TTVec), P(SolverParams),
+                                    P(TTVecOut), P(SolverInfo), V, sz, V]),
+        "tt_spgmres_solve_workspace": (sz, [P(TTOp), P(TTPrecond), P(TTVec), P(SolverParams)]),
         "tt_profile": (cint, [cint]),
         "tt_profile_read": (cint, [cint, P(dbl), c_i64p, P(dbl), P(dbl)]),
         "tt_launch_count": (i64, []),

@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libttsg.so")
 BUILD = os.path.join(HERE, "_build")
 SOURCES = ["api.cu", "solver.cu", "tt_ops.cu", "gemm_simt.cu", "gemm_tc.cu", "qr.cu", "svd.cu",
-           "lstsq.cu", "kernels.cu", "prof.cu", "noalloc.cu", "chol.cu", "adjoint.cu", "stta.cu"]
+           "lstsq.cu", "kernels.cu", "prof.cu", "noalloc.cu", "chol.cu", "adjoint.cu", "stta.cu", "precond.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

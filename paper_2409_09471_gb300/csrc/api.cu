@@ -630,14 +630,38 @@ SolveParams to_params(const tt_solver_params* p) {
   return q;
 }
 
+PrecondArgs view_precond(const tt_precond* P, int d, bool dry) {
+  if (!P) throw Error(TT_ERR_ARG, "precond: null descriptor");
+  if (P->zeta < 1 || P->zeta > TT_MAX_PRECOND_TERMS)
+    throw Error(TT_ERR_ARG, "precond: zeta out of range");
+  if (!P->alpha || !P->beta || !P->A1d) throw Error(TT_ERR_ARG, "precond: null array");
+  for (int i = 0; i < P->zeta; ++i)
+    if (!(P->beta[i] > 0.0)) throw Error(TT_ERR_ARG, "precond: beta_i > 0 required");
+  if (!dry)
+    for (int k = 0; k < d; ++k)
+      if (!P->A1d[k]) throw Error(TT_ERR_ARG, "precond: null matrix pointer");
+  PrecondArgs a;
+  a.zeta = P->zeta;
+  a.alpha = P->alpha;
+  a.beta = P->beta;
+  a.A1d = P->A1d;
+  return a;
+}
+
 void do_solve(const tt_op* A, const tt_vec* b, const tt_solver_params* p, const tt_vec_out* x,
-              tt_solver_info* info, void* ws, size_t bytes, void* stream, bool dry) {
+              tt_solver_info* info, void* ws, size_t bytes, void* stream, bool dry,
+              const tt_precond* P = nullptr) {
   SolveParams q = to_params(p);
   check_mode(p->mode);
   TTop<double> a = view_op<double>(A, 0);
   TTv<double> bv = view<double>(b, "b");
   if (a.d != bv.d) throw Error(TT_ERR_ARG, "solve: d mismatch");
   same_modes(a.n, bv.n, bv.d, "solve");
+  PrecondArgs pa;
+  if (P) {
+    pa = view_precond(P, bv.d, dry);
+    q.pre = &pa;
+  }
   TTv<double> xv;
   int64_t cap[MAXD + 1];
   const int64_t r_sol = q.r_sol > 0 ? q.r_sol : q.rmax;
@@ -678,6 +702,105 @@ void do_solve(const tt_op* A, const tt_vec* b, const tt_solver_params* p, const 
                                           " cycles");
 }
 }  // namespace
+
+size_t tt_spgmres_solve_workspace(const tt_op* A, const tt_precond* P, const tt_vec* b,
+                                  const tt_solver_params* p) {
+  return measure([&] { do_solve(A, b, p, nullptr, nullptr, nullptr, 0, nullptr, true, P); });
+}
+
+int tt_spgmres_solve(const tt_op* A, const tt_precond* P, const tt_vec* b,
+                     const tt_solver_params* p, const tt_vec_out* x, tt_solver_info* info,
+                     void* ws, size_t ws_bytes, void* stream) {
+  return guarded([&] {
+    if (!P) throw Error(TT_ERR_ARG, "spgmres: null preconditioner");
+    do_solve(A, b, p, x, info, ws, ws_bytes, stream, false, P);
+  });
+}
+
+int tt_exp_sum_coefficients(double a, double b, double tol, int cap, double* alpha,
+                            double* beta) {
+  return exp_sum_coefficients(a, b, tol, cap, alpha, beta);
+}
+
+namespace ttsg {
+namespace {
+template <typename T>
+void do_precond_apply(int mode, const tt_precond* P, const tt_vec* x, double eps, int64_t rmax,
+                      int64_t p, uint64_t seed, const tt_vec_out* y, void* ws, size_t bytes,
+                      void* stream, bool dry) {
+  TTv<T> xv = view<T>(x, "x");
+  const int d = xv.d;
+  if (d < 2) throw Error(TT_ERR_ARG, "precond: d >= 2");
+  if (!(eps >= 0.0) || rmax < 1 || p < 0)
+    throw Error(TT_ERR_ARG, "precond: eps >= 0, rmax >= 1, p >= 0");
+  PrecondArgs pa = view_precond(P, d, dry);
+  // sketch ranks of the zeta-term sum: the output capacity must cover them
+  std::vector<const int64_t*> tr(pa.zeta, xv.r);
+  int64_t ell[MAXD + 1];
+  rto_ranks(tr, xv.n, d, rmax, p, ell);
+  DRMSource<T> ds;
+  ds.seed = seed;
+  for (int k = 0; k <= d; ++k) ds.L[k] = (k == 0 || k == d) ? 1 : rmax + p;
+  TTv<T> yv;
+  int64_t cap[MAXD + 1];
+  if (dry) {
+    yv.d = d;
+    for (int k = 0; k < d; ++k) yv.n[k] = xv.n[k];
+  } else {
+    yv = view_out<T>(y, "y", cap);
+    if (yv.d != d) throw Error(TT_ERR_ARG, "precond: output d mismatch");
+    for (int k = 1; k < d; ++k)
+      if (cap[k] < std::min<int64_t>(rmax, ell[k]))
+        throw Error(TT_ERR_ARG, "precond: output capacity below min(rmax, sketch rank)");
+  }
+  Carved cv = carve(mode, ws, bytes, stream, dry);
+  fix_ctx(cv);
+  reset_flags(cv);
+  PrecondDev<T> pd;
+  precond_setup<T>(cv.ctx, pa, d, xv.n, pd);
+  std::vector<TTv<T>> bufs(pa.zeta);
+  for (auto& b : bufs) {
+    b.d = d;
+    for (int k = 0; k <= d; ++k) b.r[k] = xv.r[k];
+    for (int k = 0; k < d; ++k) {
+      b.n[k] = xv.n[k];
+      b.core[k] = cv.ar.take<T>(xv.core_elems(k));
+    }
+  }
+  precond_apply_dev<T>(cv.ctx, pd, xv, eps, rmax, p, ds, bufs, yv);
+  if (dry) throw (size_t)cv.ar.peak;
+  if (!g_dry_run) TT_CUDA(cudaStreamSynchronize(cv.ctx.st));
+  for (int k = 0; k <= d; ++k) y->rank[k] = yv.r[k];
+}
+}  // namespace
+}  // namespace ttsg
+
+size_t tt_precond_apply_workspace(int mode, const tt_precond* P, const tt_vec* x, int64_t rmax,
+                                  int64_t oversample) {
+  return measure([&] {
+    check_mode(mode);
+    if (mode == TT_MODE_FP64)
+      do_precond_apply<double>(mode, P, x, 0.1, rmax, oversample, 0, nullptr, nullptr, 0,
+                               nullptr, true);
+    else
+      do_precond_apply<float>(mode, P, x, 0.1, rmax, oversample, 0, nullptr, nullptr, 0,
+                              nullptr, true);
+  });
+}
+
+int tt_precond_apply(int mode, const tt_precond* P, const tt_vec* x, double eps, int64_t rmax,
+                     int64_t oversample, uint64_t seed, const tt_vec_out* y, void* ws,
+                     size_t ws_bytes, void* stream) {
+  return guarded([&] {
+    check_mode(mode);
+    if (mode == TT_MODE_FP64)
+      do_precond_apply<double>(mode, P, x, eps, rmax, oversample, seed, y, ws, ws_bytes, stream,
+                               false);
+    else
+      do_precond_apply<float>(mode, P, x, eps, rmax, oversample, seed, y, ws, ws_bytes, stream,
+                              false);
+  });
+}
 
 size_t tt_sgmres_solve_workspace(const tt_op* A, const tt_vec* b, const tt_solver_params* p) {
   return measure([&] { do_solve(A, b, p, nullptr, nullptr, nullptr, 0, nullptr, true); });

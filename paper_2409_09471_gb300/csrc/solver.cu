@@ -279,6 +279,23 @@ SolveResult sgmres_solve(const Ctx& c0, const TTop<double>& A64in, const TTv<dou
     copy_tt(xn, x, nullptr, 0);
   };
 
+  // ---- right preconditioning (Algorithm 5): w = A P^{-1} v_k, and each
+  // cycle's correction P^{-1} Round(sum_i y_i v_i); every application of
+  // P^{-1} is rounded to the basis (or solution) rank cap
+  const bool use_pre = p.pre != nullptr;
+  TT_CHECK_ARG(!(use_pre && use_stta), "solve: preconditioning with final_stta is not supported");
+  PrecondDev<T> pd;
+  std::vector<TTv<T>> pbufs;
+  TTv<T> z, e2;
+  if (use_pre) {
+    precond_setup<T>(c, *p.pre, d, n, pd);
+    std::vector<int64_t> pcap(d + 1);
+    for (int k = 0; k <= d; ++k) pcap[k] = std::max(vcap[k], xcap[k]);
+    for (int i = 0; i < pd.zeta; ++i) pbufs.push_back(alloc_tt<T>(ar, d, n, pcap.data()));
+    z = alloc_tt<T>(ar, d, n, vcap.data());
+    e2 = alloc_tt<T>(ar, d, n, xcap.data());
+  }
+
   if (g_dry_run) {
     // workspace query: run every scratch-using step once at capacity ranks
     for (auto& v : V) for (int q = 0; q <= d; ++q) v.r[q] = vcap[q];
@@ -303,6 +320,10 @@ SolveResult sgmres_solve(const Ctx& c0, const TTop<double>& A64in, const TTv<dou
     if (use_stta) {
       stta_sketch_basis(0);
       stta_update_x(p.maxit, 0.1, true);
+    }
+    if (use_pre) {
+      precond_apply_dev<T>(c, pd, V[0], 0.1, p.rmax, p.oversample, drm, pbufs, z);
+      precond_apply_dev<T>(c, pd, e, 0.1, r_sol, p.oversample, drm, pbufs, e2);
     }
     return res;
   }
@@ -333,9 +354,14 @@ SolveResult sgmres_solve(const Ctx& c0, const TTop<double>& A64in, const TTv<dou
     double sres = 1.0;
     for (int k = 0; k < p.maxit; ++k) {
       if (use_stta) stta_sketch_basis(k);
-      // w = A v_k
-      for (int q = 0; q <= d; ++q) w.r[q] = A64.R[q] * V[k].r[q];
-      tt_matvec_dev<T>(c, A, V[k], w);
+      // w = A v_k, or A P^{-1} v_k with P^{-1} v_k rounded to rmax
+      const TTv<T>* av = &V[k];
+      if (use_pre) {
+        precond_apply_dev<T>(c, pd, V[k], round_tol, p.rmax, p.oversample, drm, pbufs, z);
+        av = &z;
+      }
+      for (int q = 0; q <= d; ++q) w.r[q] = A64.R[q] * av->r[q];
+      tt_matvec_dev<T>(c, A, *av, w);
       // W[:, k] = S w
       tt_sketch_dev<T>(c, w, s, (const T* const*)S.data(), Wm + k * s);
       // h_{i,k} = <w, v_i> for the last ell basis vectors (Sec. 3.5), then
@@ -395,12 +421,18 @@ SolveResult sgmres_solve(const Ctx& c0, const TTop<double>& A64in, const TTv<dou
       }
       tt_round_rand_dev<T>(c, terms, final_tol, r_sol, p.oversample, drm, e);
     }
+    // right preconditioning: the correction is P^{-1} e
+    TTv<T>* ec = &e;
+    if (use_pre) {
+      precond_apply_dev<T>(c, pd, e, final_tol, r_sol, p.oversample, drm, pbufs, e2);
+      ec = &e2;
+    }
     // x <- Round(x + e) in FP64
     if (!have_x) {
-      copy_tt(e, x, nullptr, 0);
+      copy_tt(*ec, x, nullptr, 0);
       have_x = true;
     } else {
-      copy_tt(e, e64, nullptr, 0);
+      copy_tt(*ec, e64, nullptr, 0);
       std::vector<Term<double>> terms(2);
       terms[0].X = x;
       terms[1].X = e64;

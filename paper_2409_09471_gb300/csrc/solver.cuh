@@ -18,6 +18,7 @@ struct SolveParams {
   int max_restarts = 5;
   int final_stta = 0;
   int ell = 1;
+  const PrecondArgs* pre = nullptr;  // right preconditioner (Algorithm 5), or none
 };
 
 struct SolveResult {

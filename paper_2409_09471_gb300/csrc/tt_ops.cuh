@@ -76,6 +76,34 @@ void tt_stta_recover_dev(const Ctx& c, int d, const int64_t* n, const int64_t* r
 void stta_combine(const double* S, int64_t ssz, int k, const double* y, double* out,
                   cudaStream_t st);
 
+// Exponential-sum preconditioner (see tt_precond_apply): host description
+// (coefficients, device pointers to the 1-D FP64 matrices A_k) and its device
+// form (the matrices exp(-beta_i A_k) in the working precision).
+constexpr int TT_MAX_PRECOND_TERMS = 256;
+struct PrecondArgs {
+  int zeta = 0;
+  const double* alpha = nullptr;      // host [zeta]
+  const double* beta = nullptr;       // host [zeta]
+  const double* const* A1d = nullptr; // host array of d device pointers
+};
+template <typename T>
+struct PrecondDev {
+  int zeta = 0, d = 0;
+  std::vector<double> alpha;
+  std::vector<T*> E;  // E[i * d + k] = exp(-beta_i A_k), n_k x n_k row-major
+};
+// Coefficients of the exponential sum for 1/z on [a, b] at relative accuracy
+// tol; returns the number of terms (written only when it is <= cap), or -1.
+int exp_sum_coefficients(double a, double b, double tol, int cap, double* alpha, double* beta);
+template <typename T>
+void precond_setup(const Ctx& c, const PrecondArgs& P, int d, const int64_t* n,
+                   PrecondDev<T>& out);
+// y = Round(P^{-1} x) to eps and rmax; bufs: zeta TT buffers with capacity >= x's ranks.
+template <typename T>
+void precond_apply_dev(const Ctx& c, const PrecondDev<T>& P, const TTv<T>& x, double eps,
+                       int64_t rmax, int64_t oversample, const DRMSource<T>& drm,
+                       std::vector<TTv<T>>& bufs, TTv<T>& y);
+
 // Sketch ranks l_mu of the randomized rounding (see tt_round_rand).
 void rto_ranks(const std::vector<const int64_t*>& term_ranks, const int64_t* n, int d,
                int64_t rmax, int64_t oversample, int64_t* ells);

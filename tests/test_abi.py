@@ -170,3 +170,56 @@ def test_stta_entry_points_validate_and_size_on_the_host(built_lib):
     assert b"l_k >= r_k" in lib.tt_last_error()
     assert lib.tt_stta_recover(d, n, r, ok, None, None, 0.0, None, None, 0, None) == 1
     assert lib.tt_stta_sketch(0, None, 1.0, 0, None, None, None, None, None, 0, None) == 1
+
+
+def test_exp_sum_coefficients_match_the_oracle(built_lib):
+    # the library's host coefficients and the oracle's are independent codes
+    # of the same rule (trapezoidal rule on the Laplace integral of 1/z)
+    import numpy as np
+    import paper_2409_09471_gb300 as g
+    from oracle import precond as opc
+    for a, b, tol in [(1.0, 100.0, 1e-2), (39.4, 1.1e4, 1e-4), (2.0, 3e6, 1e-8)]:
+        al, be = g.exp_sum_coefficients(a, b, tol)
+        ao, bo = opc.exp_sum_coefficients(a, b, tol)
+        assert al.shape == ao.shape
+        assert np.allclose(al, ao, rtol=1e-13, atol=0) and np.allclose(be, bo, rtol=1e-13, atol=0)
+    from paper_2409_09471_gb300 import _abi
+    assert _abi.lib.tt_exp_sum_coefficients(2.0, 1.0, 1e-2, 0, None, None) == -1
+    assert _abi.lib.tt_exp_sum_coefficients(1.0, 2.0, 1.5, 0, None, None) == -1
+
+
+def test_precond_entry_points_validate_and_size_on_the_host(built_lib):
+    from paper_2409_09471_gb300 import _abi
+    lib = _abi.lib
+    d, ns = 3, [8, 8, 8]
+    n = (ctypes.c_int64 * d)(*ns)
+    r = (ctypes.c_int64 * (d + 1))(1, 3, 4, 1)
+    xc = (ctypes.c_void_p * d)(*([0x1000] * d))
+    x = _abi.TTVec(d, n, r, xc)
+    alpha = (ctypes.c_double * 5)(1.0, 0.5, 0.25, 0.1, 0.05)
+    beta = (ctypes.c_double * 5)(0.01, 0.02, 0.04, 0.08, 0.16)
+    mats = (ctypes.c_void_p * d)(*([0x3000] * d))
+    P = _abi.TTPrecond(5, alpha, beta, mats)
+    for mode in (0, 1, 2):
+        assert lib.tt_precond_apply_workspace(mode, ctypes.byref(P), ctypes.byref(x), 6, 2) > 0, \
+            lib.tt_last_error()
+    bad = _abi.TTPrecond(0, alpha, beta, mats)
+    assert lib.tt_precond_apply_workspace(0, ctypes.byref(bad), ctypes.byref(x), 6, 2) == 0
+    assert b"zeta" in lib.tt_last_error()
+    negb = (ctypes.c_double * 5)(0.01, -0.02, 0.04, 0.08, 0.16)
+    bad2 = _abi.TTPrecond(5, alpha, negb, mats)
+    assert lib.tt_precond_apply_workspace(0, ctypes.byref(bad2), ctypes.byref(x), 6, 2) == 0
+    # the preconditioned solve's workspace query is a host dry run too
+    R = (ctypes.c_int64 * (d + 1))(1, 2, 2, 1)
+    opc = (ctypes.c_void_p * d)(*([0x2000] * d))
+    op = _abi.TTOp(d, n, R, opc)
+    for mode in (0, 2):
+        p = _abi.SolverParams(20, 40, 1e-6, 0.0, 0.1, 0.1, 16, 16, 4, 0, 2, mode)
+        plain = lib.tt_sgmres_solve_workspace(ctypes.byref(op), ctypes.byref(x), ctypes.byref(p))
+        pre = lib.tt_spgmres_solve_workspace(ctypes.byref(op), ctypes.byref(P), ctypes.byref(x),
+                                             ctypes.byref(p))
+        assert pre > plain > 0, lib.tt_last_error()
+        ps = _abi.SolverParams(20, 40, 1e-6, 0.0, 0.1, 0.1, 16, 16, 4, 0, 2, mode, 1)
+        assert lib.tt_spgmres_solve_workspace(ctypes.byref(op), ctypes.byref(P), ctypes.byref(x),
+                                              ctypes.byref(ps)) == 0
+        assert b"final_stta" in lib.tt_last_error()
