@@ -53,7 +53,7 @@ extern "C" {
 #define TT_ERR_CUDA 3          /* a CUDA runtime call or kernel failed */
 #define TT_ERR_TIMEOUT 4       /* a bounded device-side wait expired */
 #define TT_ERR_NOT_CONVERGED 5 /* solver stopped at maxit / restarts; x is returned */
-#define TT_ERR_UNSUPPORTED 6   /* mode or size not supported by this build */
+#define TT_ERR_UNSUPPORTED 6   /* mode or size the library does not support */
 
 #define TT_MODE_FP64 0
 #define TT_MODE_FP32 1
