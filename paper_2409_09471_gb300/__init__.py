@@ -324,9 +324,12 @@ class Precond:
         self.beta = np.ascontiguousarray(beta, dtype=np.float64)
         if self.alpha.shape != self.beta.shape or self.alpha.ndim != 1:
             raise ValueError("alpha and beta: equal-length vectors")
+        # device float64 copies (a host tensor or array is moved to the GPU)
         self.mats = [torch.as_tensor(m, dtype=torch.float64, device="cuda").contiguous()
-                     if not isinstance(m, torch.Tensor) else m.to(torch.float64).contiguous()
                      for m in mats]
+        for m in self.mats:
+            if m.dim() != 2 or m.shape[0] != m.shape[1]:
+                raise ValueError("preconditioner matrices must be square")
 
     @classmethod
     def for_interval(cls, a: float, b: float, tol: float, mats):
