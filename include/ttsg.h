@@ -392,6 +392,8 @@ size_t tt_stta_recover_workspace(int d, const int64_t* n, const int64_t* r, cons
  *   P^{-1} = sum_i alpha_i (exp(-beta_i A_1) x .. x exp(-beta_i A_d)) ~ A_0^{-1}.
  * zeta: number of terms (1..256); alpha, beta: host arrays [zeta]; A1d: host
  * array of d device pointers to the n_k x n_k row-major FP64 matrices A_k.
+ * The descriptor carries no sizes: matrix k must have n_k x n_k entries for the
+ * n_k of the TT vectors it is applied to (the caller's responsibility).
  */
 typedef struct {
   int zeta;

@@ -249,6 +249,7 @@ def tt_sgmres_solve(op, b: TT, maxit: int, tol: float, rmax: int, mode: int = MO
     bd, k2 = b._desc()
     dev = b.cores[0].device
     if precond is not None:
+        precond.check_modes(b.ns)
         pdesc, k3 = precond._desc()
         need = lib.tt_spgmres_solve_workspace(ctypes.byref(od), ctypes.byref(pdesc),
                                               ctypes.byref(bd), ctypes.byref(p))
@@ -337,6 +338,11 @@ class Precond:
         alpha, beta = exp_sum_coefficients(a, b, tol)
         return cls(alpha, beta, mats)
 
+    def check_modes(self, ns):
+        """The C descriptor carries no sizes: matrix k must be n_k x n_k."""
+        if len(self.mats) != len(ns) or any(m.shape[0] != n for m, n in zip(self.mats, ns)):
+            raise ValueError("preconditioner matrices must be n_k x n_k for every mode k")
+
     def _desc(self):
         ap = self.alpha.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
         bp = self.beta.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
@@ -362,6 +368,7 @@ def tt_precond_apply(P: Precond, x: TT, eps: float, rmax: int, oversample: int =
                      seed: int = 0, mode: int = MODE_FP64, stream=None) -> TT:
     """``Round(P^{-1} x)`` to ``eps`` and ranks ``<= rmax``."""
     _check_dtype(x.cores, mode)
+    P.check_modes(x.ns)
     d, ns, dev, dt = x.d, x.ns, x.cores[0].device, x.cores[0].dtype
     cap = [1] + [int(rmax)] * (d - 1) + [1]
     ycores = [torch.empty(cap[k] * ns[k] * cap[k + 1], dtype=dt, device=dev) for k in range(d)]
