@@ -436,6 +436,16 @@ def tt_stta_recover(psi: Sequence[torch.Tensor], omega: Sequence[torch.Tensor],
     pseudo-inverse with relative cutoff ``rcond`` (0: 1e-12)."""
     d = len(psi)
     dev = psi[0].device
+    if len(omega) != d - 1:
+        raise ValueError("stta_recover: d - 1 omega matrices expected")
+    for t in list(psi) + list(omega):
+        if t.dtype != torch.float64 or t.device.type != "cuda":
+            raise ValueError("stta_recover: float64 CUDA tensors expected")
+    if psi[0].shape[0] != 1 or psi[-1].shape[2] != 1:
+        raise ValueError("stta_recover: boundary ranks must be 1")
+    for k in range(d - 1):
+        if tuple(omega[k].shape) != (psi[k + 1].shape[0], psi[k].shape[2]):
+            raise ValueError("stta_recover: omega[k] must be l_{k+1} x r_{k+1}")
     n = [p.shape[1] for p in psi]
     l = [1] + [p.shape[0] for p in psi[1:]] + [1]
     r = [1] + [p.shape[2] for p in psi[:-1]] + [1]
