@@ -101,13 +101,13 @@ chol_kernel(const __grid_constant__ CholBatch cb, double rel_shift, int* err) {
 }
 
 int sm_count() {
-  static int sms = 0;
-  if (!sms) {
-    int dev = 0;
+  // thread-safe one-time query (batched solves call this from several threads)
+  static const int sms = [] {
+    int dev = 0, v = 0;
     cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (sms <= 0) sms = 1;
-  }
+    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+    return v > 0 ? v : 1;
+  }();
   return sms;
 }
 
@@ -128,12 +128,12 @@ void gram_f64(const void* Y, int y_f64, int64_t m, int64_t l, int64_t sr, int64_
   P = ceil_div(m, rows);
   if ((size_t)P * l * l * sizeof(double) > ws_bytes)
     throw Error(TT_ERR_WORKSPACE, "gram_f64: workspace too small");
-  static bool attr = false;
-  if (!attr) {
+  static const bool attr = [] {
     TT_CUDA(cudaFuncSetAttribute(gram_partial_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  210 * 1024));
-    attr = true;
-  }
+    return true;
+  }();
+  (void)attr;
   const int tok = prof_begin(PROF_GRAM, st);
   gram_partial_kernel<<<(unsigned)P, GT, (size_t)rows * l * sizeof(double), st>>>(
       Y, y_f64, m, (int)l, sr, sc, rows, (double*)ws);
@@ -156,12 +156,12 @@ void chol_f64_batched(int count, const double* const* G, const int64_t* l, doubl
   }
   const size_t smem = (size_t)lmax * lmax * sizeof(double);
   if (smem > 220 * 1024) throw Error(TT_ERR_UNSUPPORTED, "chol_f64: l too large");
-  static bool attr = false;
-  if (!attr) {
+  static const bool attr = [] {
     TT_CUDA(cudaFuncSetAttribute(chol_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  220 * 1024));
-    attr = true;
-  }
+    return true;
+  }();
+  (void)attr;
   const int tok = prof_begin(PROF_CHOL, st);
   chol_kernel<<<count, GT, smem, st>>>(cb, rel_shift, err_flag);
   check_launch("chol_kernel");

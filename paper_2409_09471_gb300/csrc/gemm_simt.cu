@@ -189,13 +189,13 @@ __global__ void splitk_reduce_kernel(const __grid_constant__ GemmGroup g,
 }
 
 int gemm_num_sms() {
-  static int sms = 0;
-  if (!sms) {
-    int dev = 0;
+  // thread-safe one-time query (batched solves call this from several threads)
+  static const int sms = [] {
+    int dev = 0, v = 0;
     cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (sms <= 0) sms = 1;
-  }
+    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+    return v > 0 ? v : 1;
+  }();
   return sms;
 }
 

@@ -143,12 +143,12 @@ void lstsq_add_column(const double* W, const double* c, int64_t s, int64_t k, in
   LSState S = carve(ws, s, kmax);
   const size_t smem = sizeof(double) * (2 * s + kmax);
   if (smem > 200 * 1024) throw Error(TT_ERR_UNSUPPORTED, "lstsq: sketch size too large");
-  static bool attr = false;
-  if (!attr) {
+  static const bool attr = [] {
     TT_CUDA(cudaFuncSetAttribute(ls_step_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  200 * 1024));
-    attr = true;
-  }
+    return true;
+  }();
+  (void)attr;
   ls_step_kernel<<<1, LS_THREADS, smem, st>>>(W, c, (int)s, (int)k, (int)kmax, S, y, res);
   check_launch("ls_step_kernel");
 }

@@ -630,25 +630,26 @@ void jacobi_svd_batched(const JacobiBatchArgs& a, cudaStream_t st) {
   if (smem > 220 * 1024)
     throw Error(TT_ERR_UNSUPPORTED, "jacobi_svd: l = " + std::to_string(lmax) + " too large for " +
                                         (a.f32 ? "FP32" : "FP64"));
-  static bool attr[2] = {false, false};
   // PPW column pairs per warp
   const int pairs = (int)((lmax + 1) / 2);
   const int threads =
       (int)std::min<int64_t>(SVD_THREADS, std::max<int64_t>(64, ceil_div(pairs, PPW) * 32));
   const int tok = prof_begin(PROF_SVD, st);
   if (a.f32) {
-    if (!attr[0]) {
+    static const bool attr_f = [] {
       TT_CUDA(cudaFuncSetAttribute(jacobi_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    220 * 1024));
-      attr[0] = true;
-    }
+      return true;
+    }();
+    (void)attr_f;
     jacobi_kernel<float><<<a.count, threads, smem, st>>>(jb, a.err);
   } else {
-    if (!attr[1]) {
+    static const bool attr_d = [] {
       TT_CUDA(cudaFuncSetAttribute(jacobi_kernel<double>,
                                    cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024));
-      attr[1] = true;
-    }
+      return true;
+    }();
+    (void)attr_d;
     jacobi_kernel<double><<<a.count, threads, smem, st>>>(jb, a.err);
   }
   check_launch("jacobi_kernel");
