@@ -12,14 +12,14 @@ struct Rec {
   double flops, bytes;
 };
 std::mutex g_mu;
-int g_mask = 0;
+std::atomic<int> g_mask{0};  // read by every launch wrapper, without the lock
 std::vector<Rec> g_recs;
 }  // namespace
 
 std::atomic<long long> g_launches{0};
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
-bool prof_on(int cls) { return !g_dry_run && (g_mask >> cls) & 1; }
+bool prof_on(int cls) { return !g_dry_run && (g_mask.load(std::memory_order_relaxed) >> cls) & 1; }
 
 int prof_begin(int cls, cudaStream_t st) {
   if (!prof_on(cls)) return -1;
@@ -52,7 +52,7 @@ int tt_profile(int mask) {
     cudaEventDestroy(r.b);
   }
   g_recs.clear();
-  g_mask = mask;
+  g_mask.store(mask);
   return TT_OK;
 }
 
