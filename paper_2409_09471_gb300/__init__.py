@@ -416,6 +416,13 @@ def tt_stta_sketch(x: TT, X: TT, Y: TT, mode: int = MODE_FP64, coef: float = 1.0
     else:
         psi, omega = out
         acc = 1
+        want_p = [(l[k], x.ns[k], r[k + 1]) for k in range(x.d)]
+        want_o = [(l[k + 1], r[k + 1]) for k in range(x.d - 1)]
+        if ([tuple(t.shape) for t in psi] != want_p or [tuple(t.shape) for t in omega] != want_o
+                or any(t.dtype != torch.float64 or t.device.type != "cuda" or
+                       not t.is_contiguous() for t in list(psi) + list(omega))):
+            raise ValueError("stta_sketch: out must hold contiguous float64 CUDA sketches of "
+                             "the shapes this x, X, Y give")
     xd, k1 = x._desc()
     Xd, k2 = X._desc()
     Yd, k3 = Y._desc()
