@@ -171,6 +171,29 @@ def sketch_dense(xfull, S):
     return out
 
 
+def sketch_tt_rows(cores, Y):
+    """Sketch whose row j is a TT tensor of its own (rank R > 1 generalises the
+    Khatri-Rao rows, which are rank 1): ``(S x)_j = <Y_j, x>`` by the Gram sweep
+    ``Z_k = sum_i Y_k[j, :, i, :]^T Z_{k-1} C_k[:, i, :]``.  ``Y[k]`` has shape
+    ``[s][R_{k-1}][n_k][R_k]`` (R_0 = R_d = 1).  Not in the paper: reading
+    beyond the Khatri-Rao sketch, for a sketch that still embeds at large d."""
+    s = Y[0].shape[0]
+    out = np.zeros(s)
+    for j in range(s):
+        Z = np.ones((1, 1))
+        for Yk, C in zip(Y, cores):
+            Z = sum(Yk[j, :, i, :].T @ Z @ C[:, i, :] for i in range(C.shape[1]))
+        out[j] = Z[0, 0]
+    return out
+
+
+def sketch_tt_rows_dense(xfull, Y):
+    """Row j of the TT-row sketch formed explicitly as the full tensor of the
+    TT ``Y_j`` and applied to the dense vector."""
+    s = Y[0].shape[0]
+    return np.array([full([Yk[j] for Yk in Y]) @ xfull for j in range(s)])
+
+
 def left_orthogonalize(cores):
     """QR sweep left to right; returns cores 1..d-1 left-orthogonal and the
     represented tensor unchanged."""

@@ -139,3 +139,31 @@ def test_bad_inputs_raise():
         tt.check_tt([x[0][:, :, :1], x[1]])
     with pytest.raises(ValueError):
         ti.random_tt([3, 3], [2, 2, 1], seed=0)
+
+
+def test_tt_row_sketch_rank1_is_khatri_rao():
+    # rank-1 rows are Khatri-Rao rows: the same factors give the same sketch
+    ns = [4, 3, 5, 2]
+    x = ti.random_tt(ns, [1, 2, 3, 2, 1], seed=21)
+    S = ti.khatri_rao_factors(ns, 9, seed=22)
+    Y = [Sk[:, None, :, None] for Sk in S]
+    assert np.allclose(tt.sketch_tt_rows(x, Y), tt.sketch_kr(x, S), rtol=1e-13, atol=1e-15)
+
+
+def test_tt_row_sketch_against_dense_rows():
+    ns = [3, 4, 3]
+    x = ti.random_tt(ns, [1, 2, 3, 1], seed=23)
+    Y = ti.tt_row_sketch(ns, 7, 3, seed=24)
+    assert np.allclose(tt.sketch_tt_rows(x, Y), tt.sketch_tt_rows_dense(tt.full(x), Y),
+                       rtol=1e-12, atol=1e-14)
+
+
+def test_tt_row_sketch_preserves_norms_in_expectation():
+    # E ||S x||^2 = ||x||^2: the mean over 400 independent sketches is within
+    # five standard errors of 1
+    ns = [3, 3, 3, 3]
+    x = ti.random_tt(ns, [1, 2, 2, 2, 1], seed=25)
+    nx = tt.norm(x) ** 2
+    r = np.array([np.sum(tt.sketch_tt_rows(x, ti.tt_row_sketch(ns, 4, 3, seed=100 + t)) ** 2) / nx
+                  for t in range(400)])
+    assert abs(r.mean() - 1.0) <= 5 * r.std() / np.sqrt(len(r))

@@ -144,6 +144,23 @@ def khatri_rao_factors(ns, s: int, seed: int) -> list:
     return [rng.standard_normal((s, n)) * std for n in ns]
 
 
+def tt_row_sketch(ns, s: int, R: int, seed: int) -> list:
+    """Cores ``[s][R_{k-1}][n_k][R_k]`` of s independent Gaussian TT rows of
+    rank R (R_0 = R_d = 1): entries N(0, 1/R_k), the first core scaled by
+    ``s^{-1/2}``, so that ``E ||S x||^2 = ||x||^2``.  R = 1 gives Khatri-Rao rows."""
+    rng = np.random.default_rng(seed)
+    d = len(ns)
+    out = []
+    for k, n in enumerate(ns):
+        a = 1 if k == 0 else R
+        b = 1 if k == d - 1 else R
+        Yk = rng.standard_normal((s, a, n, b)) / np.sqrt(b)
+        if k == 0:
+            Yk = Yk / np.sqrt(s)
+        out.append(Yk)
+    return out
+
+
 def gaussian_drm(ns, ells, seed: int) -> list:
     """Gaussian TT-DRM cores ``[l_{k-1}, n_k, l_k]`` with variance
     ``1/(l_{k-1} n_k l_k)`` (Definition "Random Gaussian TT-Tensor").
