@@ -289,7 +289,7 @@ typedef struct {
                          for TT_MODE_FP64: in the float modes its refinement converged
                          far more slowly than the default); 0: randomized rounding of
                          the stored basis (default) */
-  int ell;            /* incomplete orthogonalisation (Alg. 4, Sec. 3.5): v~ = Round(w -
+  int ell;            /* incomplete orthogonalisation (Alg. 4, Sec. 3.4): v~ = Round(w -
                          sum of h_{i,k} v_i over the last ell basis vectors); 0 => 1 */
 } tt_solver_params;
 
@@ -387,7 +387,7 @@ int tt_stta_recover(int d, const int64_t* n, const int64_t* r, const int64_t* l,
 size_t tt_stta_recover_workspace(int d, const int64_t* n, const int64_t* r, const int64_t* l);
 
 /*
- * Exponential-sum right preconditioning (Sec. 3.7, Alg. 5) of an operator whose
+ * Exponential-sum right preconditioning (Sec. 4.1, Alg. 5) of an operator whose
  * dominant part is a Kronecker sum A_0 = sum_k (I x .. x A_k x .. x I):
  *   P^{-1} = sum_i alpha_i (exp(-beta_i A_1) x .. x exp(-beta_i A_d)) ~ A_0^{-1}.
  * zeta: number of terms (1..256); alpha, beta: host arrays [zeta]; A1d: host
@@ -430,7 +430,7 @@ size_t tt_precond_apply_workspace(int mode, const tt_precond* P, const tt_vec* x
 /*
  * tt_spgmres_solve - right-preconditioned TT-sGMRES (TT-sPGMRES, Alg. 5): as
  * tt_sgmres_solve, with w = A P^{-1} v_k (P^{-1} v_k rounded to rmax, the
- * bounded-rank rounding of Sec. 3.8) and each cycle's correction
+ * bounded-rank rounding of Sec. 4.2) and each cycle's correction
  * P^{-1} Round(sum_i y_i v_i) rounded to r_sol.  The true residual is that of
  * A x = b.  p->final_stta must be 0.
  */

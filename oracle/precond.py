@@ -1,4 +1,4 @@
-"""Exponential-sum right preconditioning and TT-sPGMRES (Section 3.7,
+"""Exponential-sum right preconditioning and TT-sPGMRES (Section 4,
 Algorithm 5), in float64.
 
 TEST INFRASTRUCTURE ONLY (see the package docstring).
@@ -76,7 +76,7 @@ def apply_precond(cores, A1d, alpha, beta, eps=None, rmax=None, drm=None, oversa
     """``P^{-1} x = sum_i alpha_i (exp(-beta_i A_1) x .. x exp(-beta_i A_d)) x``.
     Without ``drm`` the exact sum (ranks multiplied by the number of terms);
     with it, rounded by the randomized rounding to ``eps`` and ``rmax`` (the
-    bounded-rank rounding of Section 3.8)."""
+    bounded-rank rounding of Section 4.2)."""
     E = precond_matrices(A1d, alpha, beta)
     terms = [(float(a), mode_product(cores, Ei)) for a, Ei in zip(alpha, E)]
     if drm is None:

@@ -57,7 +57,7 @@ def tt_sgmres(op, b, S, drm, maxit, tol, round_tol, rmax, oversample=10,
     r_sol, final_tol : rank cap and tolerance of the final rounding.
     ell : incomplete orthogonalisation: ``h_{i,k} = w^T v_i`` for the last
         ``ell`` basis vectors and ``v~ = Round(w - sum_i h_{i,k} v_i)``
-        (Section 3.5).
+        (Section 3.4).
 
     Returns ``(x, info)`` with the sketched residual history, basis ranks, the
     number of iterations, the basis ``V`` and the coefficients ``H``

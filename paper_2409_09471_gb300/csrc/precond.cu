@@ -1,11 +1,11 @@
 // Exponential-sum right preconditioning of a Kronecker-sum operator (Section
-// 3.7, Algorithm 5):
+// 4, Algorithm 5):
 //   P^{-1} = sum_i alpha_i (exp(-beta_i A_1) x .. x exp(-beta_i A_d)),
 // an exponential sum E(z) = sum_i alpha_i exp(-beta_i z) ~ 1/z evaluated at the
 // Kronecker sum (its terms commute, so exp(-beta sum_j A_j) is the Kronecker
 // product of the exp(-beta A_j)).  Applying it to a TT vector multiplies every
 // core by exp(-beta_i A_k) along its mode index (ranks unchanged) and rounds the
-// zeta-term sum to a rank cap (the bounded-rank rounding of Section 3.8).
+// zeta-term sum to a rank cap (the bounded-rank rounding of Section 4.2).
 //
 // The coefficients come from the trapezoidal rule on 1/z = int_R exp(t - e^t z) dt
 // (Trefethen and Weideman, "The exponentially convergent trapezoidal rule",

@@ -364,7 +364,7 @@ SolveResult sgmres_solve(const Ctx& c0, const TTop<double>& A64in, const TTv<dou
       tt_matvec_dev<T>(c, A, *av, w);
       // W[:, k] = S w
       tt_sketch_dev<T>(c, w, s, (const T* const*)S.data(), Wm + k * s);
-      // h_{i,k} = <w, v_i> for the last ell basis vectors (Sec. 3.5), then
+      // h_{i,k} = <w, v_i> for the last ell basis vectors (Sec. 3.4), then
       // v~ = Round(w - sum_i h_{i,k} v_i)
       const int first = std::max(0, k - ell + 1);
       std::vector<Term<T>> terms(1 + (k - first + 1));

@@ -95,7 +95,7 @@ def test_batch_of_one_converges_like_single_solve(g):
 @pytest.mark.parametrize("mode,ell", [(0, 3), (2, 2)])
 def test_partial_orthogonalisation(g, mode, ell):
     # each new vector orthogonalised against the last ell basis vectors
-    # (Section 3.5): the restarted solve reaches the tolerance by the oracle's
+    # (Section 3.4): the restarted solve reaches the tolerance by the oracle's
     # exact FP64 residual
     w = ti.workload("convdiff", d=4, n=12, maxit=40)
     op = g.op_to_device(w.op)

@@ -1,5 +1,5 @@
 """GPU parity of the exponential-sum preconditioner and TT-sPGMRES (Section
-3.7, Algorithm 5) against the oracle: P^{-1} x at ranks where the rounding is
+4, Algorithm 5) against the oracle: P^{-1} x at ranks where the rounding is
 exact (FP64 1e-10 relative), and a preconditioned solve of a Laplacian system
 checked by the oracle's exact residual and against the dense solution."""
 import numpy as np

@@ -1,5 +1,5 @@
 """Pins of the oracle's exponential-sum preconditioner and TT-sPGMRES
-(Section 3.7, Algorithm 5): the sum against 1/z on its interval; P^{-1} by mode
+(Section 4, Algorithm 5): the sum against 1/z on its interval; P^{-1} by mode
 products against the matrix exponential of the whole Kronecker sum (scipy
 expm of the dense operator); the spectrum of P^{-1} A against the closed-form
 Laplacian eigenvalues; and the preconditioned solve against a dense solve."""

@@ -92,7 +92,7 @@ def test_full_orthogonalisation_gives_arnoldi():
     # l = maxit and no truncation (RTO at tolerance 0 with the rank cap above
     # every representation rank is exact): the basis is orthonormal and
     # A v_k = sum_{i <= k+1} h_{i,k} v_i holds (the Arnoldi relation of
-    # Section 3.5); with l = 1 the basis is not orthogonal
+    # Section 3.4); with l = 1 the basis is not orthogonal
     w = ti.workload("convdiff", d=3, n=5, rank=2)
     ns = w.ns
     S = philox.sketch_factors(ns, 20, 0)
