@@ -144,6 +144,31 @@ __global__ void sum_final(const double* part, int np, double* out) {
 
 __global__ void sqrt_kernel(const double* x, double* y) { *y = sqrt(fmax(*x, 0.0)); }
 
+// x *= 2^-e with e the binary exponent of sqrt(sum of the np partial sums of
+// squares): every CTA reduces the partials itself, then scales its share.  A
+// power of two changes no significand bit, so the scaling itself is exact.
+template <typename T>
+__global__ void pow2_scale_kernel(T* x, int64_t count, const double* part, int np) {
+  __shared__ double fac;
+  if (threadIdx.x < 32) {
+    double v = 0.0;
+    for (int i = threadIdx.x; i < np; i += 32) v += part[i];
+    v = warp_sum(v);
+    if (threadIdx.x == 0) {
+      const double s = sqrt(v);
+      // the factor itself must be finite in T
+      const int lim = sizeof(T) == 4 ? 120 : 1000;
+      const int e = (s > 0.0 && isfinite(s)) ? max(-lim, min(lim, ilogb(s))) : 0;
+      fac = ldexp(1.0, -e);
+    }
+  }
+  __syncthreads();
+  const T f = (T)fac;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < count;
+       e += (int64_t)gridDim.x * blockDim.x)
+    x[e] *= f;
+}
+
 }  // namespace
 
 void copy3d(const std::vector<CopySeg>& segs, cudaStream_t st) {
@@ -197,6 +222,16 @@ void dot_acc(const void* a, const void* b, int f64, int64_t count, double* out, 
   check_launch("dot_partial");
   sum_final<<<1, 256, 0, st>>>(scratch, np, out);
   check_launch("sum_final");
+}
+
+void pow2_normalize(void* x, int x_f64, int64_t count, double* scratch, cudaStream_t st) {
+  if (g_dry_run || count <= 0) return;
+  const int np = (int)std::min<int64_t>(std::max<int64_t>(ceil_div(count, 1024), 1), 256);
+  sumsq_partial<<<np, 256, 0, st>>>(x, x_f64, count, scratch);
+  check_launch("sumsq_partial");
+  if (x_f64) pow2_scale_kernel<double><<<np, 256, 0, st>>>((double*)x, count, scratch, np);
+  else pow2_scale_kernel<float><<<np, 256, 0, st>>>((float*)x, count, scratch, np);
+  check_launch("pow2_scale_kernel");
 }
 
 void sqrt_scalar(const double* x, double* y, cudaStream_t st) {

@@ -36,6 +36,10 @@ void sumsq(const void* x, int x_f64, int64_t count, double* out, double* scratch
 // out[0] = sum_e a[e] b[e] (FP64 accumulation); a, b both float or both double.
 void dot_acc(const void* a, const void* b, int f64, int64_t count, double* out, double* scratch,
              cudaStream_t st);
+// x <- 2^-e x with e the binary exponent of ||x||_2 (so 1 <= ||x|| < 2 after
+// it): an exact rescaling that keeps long products of small or large factors
+// inside the float range.  scratch: 256 doubles.
+void pow2_normalize(void* x, int x_f64, int64_t count, double* scratch, cudaStream_t st);
 // y[0] = sqrt(x[0]).
 void sqrt_scalar(const double* x, double* y, cudaStream_t st);
 

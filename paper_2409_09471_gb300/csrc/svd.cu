@@ -166,7 +166,12 @@ jacobi_kernel(const __grid_constant__ JacobiBatch jb, int* err) {
         if (sizeof(T) == 4) {
           const float zeta = __fdividef((float)(be - al), 2.0f * (float)ga);
           t = (T)__fdividef(zeta >= 0.f ? 1.f : -1.f, fabsf(zeta) + sqrtf(1.f + zeta * zeta));
-          c = (T)rsqrtf(1.f + (float)(t * t));
+          // t may be approximate, but c and s must satisfy c^2 + s^2 = 1 to
+          // rounding: the approximate rsqrtf (up to 2 ulp, with a bias) drifts
+          // the orthogonality of V linearly over the ~sweeps * l rotations a
+          // column takes (1e-4 at l = 72); correctly rounded sqrt and division
+          // keep the drift at the level of a random walk
+          c = (T)(1.0f / sqrtf(1.f + (float)(t * t)));
         } else {
           const T zeta = (be - al) / (T(2) * ga);
           t = (zeta >= T(0) ? T(1) : T(-1)) / (fabs(zeta) + sqrt(T(1) + zeta * zeta));
@@ -232,10 +237,53 @@ jacobi_kernel(const __grid_constant__ JacobiBatch jb, int* err) {
     sigma[rank] = sg[j];
     for (int i = 0; i < l; ++i) {
       GV[(size_t)i * l + rank] = (double)A[(size_t)j * l + i];
-      V[(size_t)i * l + rank] = (double)Vm[(size_t)j * l + i];
+      if (sizeof(T) == 8) V[(size_t)i * l + rank] = (double)Vm[(size_t)j * l + i];
     }
   }
   __syncthreads();
+  if (sizeof(T) == 4) {
+    // Single precision: the rounding errors of applying some sweeps * l
+    // rotations to every column leave V orthogonal only to ~1e-5; one
+    // Newton-Schulz step V <- V (3 I - V^T V) / 2 (quadratic, so 1e-5 -> 1e-10)
+    // restores it to the level of FP32 rounding.  M = V^T V goes where A was
+    // (GV is written out already), with compensated sums; one row of V at a
+    // time goes through the norm buffer.
+    T* M = A;
+    for (int e = tid; e < l * l; e += nthreads) {
+      const int p = e / l, q = e % l;
+      if (q < p) continue;
+      const T* vp = Vm + (size_t)p * l;
+      const T* vq = Vm + (size_t)q * l;
+      T sum = 0, comp = 0;
+      for (int i = 0; i < l; ++i) {
+        const T y = fma(vp[i], vq[i], -comp);
+        const T t2 = sum + y;
+        comp = (t2 - sum) - y;
+        sum = t2;
+      }
+      M[(size_t)p * l + q] = sum;
+      M[(size_t)q * l + p] = sum;
+    }
+    __syncthreads();
+    T* row = nrm2;
+    for (int i = 0; i < l; ++i) {
+      for (int k = tid; k < l; k += nthreads) row[k] = Vm[(size_t)k * l + i];
+      __syncthreads();
+      for (int j = tid; j < l; j += nthreads) {
+        T acc = 0;
+        for (int k = 0; k < l; ++k) acc = fma(row[k], M[(size_t)k * l + j], acc);
+        Vm[(size_t)j * l + i] = T(1.5) * row[j] - T(0.5) * acc;
+      }
+      __syncthreads();
+    }
+    for (int j = tid; j < l; j += nthreads) {
+      int rank = 0;
+      for (int i = 0; i < l; ++i)
+        if (sg[i] > sg[j] || (sg[i] == sg[j] && i < j)) ++rank;
+      for (int i = 0; i < l; ++i) V[(size_t)i * l + rank] = (double)Vm[(size_t)j * l + i];
+    }
+    __syncthreads();
+  }
   if (tid == 0) {
     double tot = 0.0;
     for (int i = 0; i < l; ++i) tot += sigma[i] * sigma[i];
@@ -425,7 +473,8 @@ jacobi_cluster_kernel(const __grid_constant__ JacobiBatch jb, int ld, int nplm, 
               t = fabsf(zeta) > 1e4f ? (T)__fdividef(0.5f, zeta)
                                      : (T)__fdividef(zeta >= 0.f ? 1.f : -1.f,
                                                      fabsf(zeta) + sqrtf(1.f + zeta * zeta));
-              c = (T)rsqrtf(1.f + (float)(t * t));
+              // correctly rounded: c^2 + s^2 = 1 to rounding (see jacobi_kernel)
+              c = (T)(1.0f / sqrtf(1.f + (float)(t * t)));
             } else {
               // the angle only needs single precision (it sets how much of
               // gamma is removed); c = 1/sqrt(1+t^2), s = c t in double keep

@@ -258,6 +258,11 @@ void tt_round_rand_dev(const Ctx& c, const std::vector<Term<T>>& terms, double e
       gemm(c.mode, p1, c.st);
       gemm(c.mode, p2, c.st);
     }
+    // The rounding's result does not depend on the scale of any W: rescale the
+    // stacked contractions of this bond by an exact power of two.  Over many
+    // cores the Gaussian DRM factors (entries ~ 1/sqrt(l n l)) would otherwise
+    // shrink W geometrically, into the subnormal range of FP32 at d = 20.
+    pow2_normalize(Wc[k], f64, Ts[k] * ell[k], c.scratch + 256, c.st);
   }
 
   // 3. left sweep: Z = M x_1 X, Y = Z W, Y = Q R, core <- Q, M = Q^T Z
@@ -423,11 +428,13 @@ void tt_round_rand_dev(const Ctx& c, const std::vector<Term<T>>& terms, double e
     }
     rh[0] = rh[d] = 1;
     // W_b = V_b[:, :r_b] in the working precision
+    // (buffers sized by the rank caps min(l_b, rmax), so that the workspace
+    // query, which cannot see the ranks, reserves the same bytes)
     std::vector<T*> W(d + 1, nullptr);
     {
       std::vector<CopySeg> segs;
       for (int b = 1; b < d; ++b) {
-        W[b] = ar.take<T>(ell[b] * rh[b]);
+        W[b] = ar.take<T>(ell[b] * std::min(ell[b], rmax));
         CopySeg sgm;
         sgm.src = Vd[b]; sgm.dst = W[b]; sgm.A = ell[b]; sgm.B = rh[b]; sgm.C = 1;
         sgm.sa = ell[b]; sgm.sb = 1; sgm.src_f64 = 1; sgm.dst_f64 = 0;
@@ -439,7 +446,7 @@ void tt_round_rand_dev(const Ctx& c, const std::vector<Term<T>>& terms, double e
     std::vector<T*> U(d, nullptr);
     std::vector<GemmProblem> p1, p2;
     for (int k = 0; k < d - 1; ++k) {
-      U[k] = (k == 0) ? y.core[0] : ar.take<T>(ell[k] * n[k] * rh[k + 1]);
+      U[k] = (k == 0) ? y.core[0] : ar.take<T>(ell[k] * n[k] * std::min(ell[k + 1], rmax));
       p1.push_back(gemm_rm((int)(ell[k] * n[k]), rh[k + 1], (int)ell[k + 1], H[k], ell[k + 1],
                            W[k + 1], rh[k + 1], U[k], rh[k + 1]));
     }
