@@ -18,7 +18,12 @@ timed interval.  With ``--gpus N`` (torchrun) every rank solves its own copy:
 the path has no data-parallel split (replicas only).
 
 ``--impl reference`` times the FP64 CPU oracle (the same algorithm in NumPy)
-on this machine's host cores on a bounded sample of the same workload.
+on this machine's host cores: every timed step is one full solve of the same
+workload (restarts, final rounding and exact residual included); the warm-up
+steps are single untimed Krylov iterations.  The GPU arm's ``cpu_baseline`` is
+one such full solve.  ``roofline`` comes from a separate pass of solves in
+which every kernel launch is bracketed by CUDA events; the headline loop runs
+without them.
 """
 from __future__ import annotations
 
@@ -40,10 +45,6 @@ import ttinputs as ti  # noqa: E402
 
 METRIC = "TT-sGMRES time-to-residual 1e-6 (s) mixed vs FP64 GPU; contraction TFLOP/s vs peak"
 WORKLOAD = "convdiff d=10 n=64 (L+10B Kronecker sum, TT rank 2), b rank 4, rmax 64, m<=80, s=160"
-# FP64 and FP32 CUDA-core peaks from the unit counts: 152 SMs x (2 FP64 | 128 FP32)
-# FMA/clk x 2 FLOP x 2.070 GHz (maximum SM clock).
-FP64_ALU_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
-FP32_ALU_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 # TF32 dense tensor peak = measured BF16 peak x nominal TF32/BF16 ratio (1.1 / 2.25)
 TF32_OVER_BF16 = 1.1 / 2.25
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the
@@ -60,8 +61,12 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--mode", choices=["tf32", "fp32", "fp64"], default=None)
     ap.add_argument("--no-fp64-leg", action="store_true")
-    ap.add_argument("--cpu-seconds", type=float, default=20.0,
-                    help="budget of the host oracle sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true",
+                    help="skip the host oracle solve of the GPU arm")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the other configurations' solves")
+    ap.add_argument("--ref-small", action="store_true",
+                    help="reference arm on a d=4, n=12 system (plumbing tests only)")
     ap.add_argument("--case", choices=["solve", "round", "batched"], default="solve",
                     help="'round': time one randomized rounding of w - h v at the workload's "
                          "sizes (the kernel-level case used for ncu captures); 'batched': the "
@@ -154,70 +159,217 @@ class Clocks:
 
 
 # ---------------------------------------------------------------- oracle
-def oracle_sample(budget_s: float, mode_note: str):
-    """Times the FP64 oracle's TT-sGMRES on the workload for as many Krylov
-    iterations as fit in ``budget_s`` (first cycle), and returns seconds per
-    iteration plus a description."""
-    from oracle import solvers as osol, philox as oph, tt as ott  # noqa: F401
-    import oracle.rounding as ornd
-    w, p = workload()
+def oracle_params(p):
+    """Solver settings of the FP64 oracle run that match the GPU solve: the
+    rounding tolerance of the first cycle (eta * stop_safety * tol) and the
+    DRM capacity the GPU draws (largest rank cap plus oversampling)."""
+    return dict(maxit=p["maxit"], tol=p["tol"], round_tol=p["eta"] * 0.1 * p["tol"],
+                rmax=p["rmax"], oversample=p["oversample"], r_sol=p["r_sol"], stop_safety=0.1,
+                max_restarts=8)
+
+
+def oracle_inputs(w, p):
+    from oracle import philox as oph
     S = oph.sketch_factors(w.ns, p["s"], 0)
-    L = p["rmax"] + p["oversample"]
+    rb = max(max(c.shape[0], c.shape[2]) for c in w.b)
+    L = max(p["rmax"], p["r_sol"], rb) + p["oversample"]
     drm = oph.drm_cores(w.ns, [1] + [L] * (w.d - 1) + [1], 0)
-    # run iterations one at a time until the budget is spent
+    return S, drm
+
+
+def oracle_full_solve(w, p):
+    """One full FP64 oracle TT-sGMRES solve of the workload on the host cores:
+    every Krylov iteration, restarts, the final rounding and the exact FP64
+    residual check, timed as a whole.  Returns (seconds, info)."""
+    from oracle import solvers as osol
+    S, drm = oracle_inputs(w, p)
     t0 = time.perf_counter()
-    beta = ott.norm(w.b)
-    v = ott.scale(w.b, 1.0 / beta)
-    Sr0 = ott.sketch_kr_fast(w.b, S)
-    Wc = []
-    its = 0
-    while True:
-        wv = ott.matvec(w.op, v)
-        Wc.append(ott.sketch_kr_fast(wv, S))
-        h = ott.dot(wv, v)
-        vt = ornd.rto_round([(1.0, wv), (-h, v)], drm, eps=p["eta"] * 1e-5, rmax=p["rmax"],
-                            oversample=p["oversample"])
-        v = ott.scale(vt, 1.0 / ott.norm(vt))
-        osol.sketched_lstsq(np.stack(Wc, axis=1), Sr0)
-        its += 1
-        if time.perf_counter() - t0 > budget_s or its >= p["maxit"]:
-            break
-    dt = time.perf_counter() - t0
-    cores = os.cpu_count()
-    return dt / its, its, cores, dt
+    _, info = osol.solve(w.op, w.b, S, drm, **oracle_params(p))
+    return time.perf_counter() - t0, info
+
+
+def oracle_warmup(w, p):
+    """One untimed Krylov iteration of the oracle (warms the BLAS threads)."""
+    from oracle import solvers as osol
+    S, drm = oracle_inputs(w, p)
+    q = oracle_params(p)
+    osol.tt_sgmres(w.op, w.b, S, drm, maxit=1, tol=q["tol"], round_tol=q["round_tol"],
+                   rmax=q["rmax"], oversample=q["oversample"], r_sol=q["r_sol"])
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count()
+
+
+def ref_workload(args):
+    """The bench workload, or (``--ref-small``, a plumbing-test option) the
+    same system at d = 4, n = 12."""
+    if args.ref_small:
+        w = ti.workload("convdiff", d=4, n=12, maxit=30)
+        return w, dict(w.params), "convdiff d=4 n=12 (plumbing test)"
+    w, p = workload()
+    return w, p, WORKLOAD
 
 
 def run_reference(args):
+    """The reference arm: the FP64 oracle (the same algorithm in NumPy), as it
+    stands, on the host cores; every timed step is one full solve."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    per_iter = []
-    its_total = 0
-    t_total = 0.0
-    budget = max(5.0, args.cpu_seconds / max(1, args.steps))
+    w, p, name = ref_workload(args)
+    for _ in range(args.warmup):
+        oracle_warmup(w, p)
+    secs, iters, res = [], [], []
     for _ in range(args.steps):
-        s, its, cores, dt = oracle_sample(budget, "reference")
-        per_iter.append(s)
-        its_total += its
-        t_total += dt
-    sec_per_iter = statistics.median(per_iter)
-    # a whole solve takes the iteration count the GPU path needs (the same
-    # algorithm); the oracle's own count for this workload is of that order
-    iters = int(os.environ.get("TTSG_REF_ITERS", "60"))
-    value = sec_per_iter * iters
+        dt, info = oracle_full_solve(w, p)
+        secs.append(dt)
+        iters.append(info["iters"])
+        res.append(info["true_res"])
+    value = statistics.mean(secs)
+    cores = host_cores()
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": value * 1e3, "higher_is_better": False, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "l2": "host run"},
+            "config": {"workload": name, "l2": "host run"},
+            "iters_per_solve": statistics.median(iters), "true_res_max": max(res),
             "cpu_baseline": {"value": value, "unit": "s", "cores": cores, "kind": "oracle",
-                             "sample": f"{its_total} Krylov iterations over {args.steps} steps "
-                                       f"({t_total:.1f} s), projected to {iters} iterations"},
+                             "sample": f"{args.steps} full FP64 oracle solves (every iteration, "
+                                       f"restarts, final rounding, exact residual); warm-up: "
+                                       f"{args.warmup} single untimed Krylov iterations"},
             "e2e": {"value": value, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
 # ---------------------------------------------------------------- GPU arm
+def measured_alu_peaks(torch):
+    """FP64 and FP32 (no TF32) GEMM rates of cuBLAS on this GPU, best of three
+    back-to-back calls each, in TFLOP/s: the CUDA-core peaks the FP64 QR and the
+    FP32 CUDA-core GEMMs are held against."""
+    out = {}
+    old = torch.backends.cuda.matmul.allow_tf32
+    torch.backends.cuda.matmul.allow_tf32 = False
+    try:
+        for name, dt, n in (("fp64", torch.float64, 4096), ("fp32", torch.float32, 8192)):
+            a = torch.randn(n, n, dtype=dt, device="cuda")
+            b = torch.randn(n, n, dtype=dt, device="cuda")
+            torch.matmul(a, b)
+            torch.cuda.synchronize()
+            best = float("inf")
+            for _ in range(3):
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record()
+                torch.matmul(a, b)
+                e1.record()
+                torch.cuda.synchronize()
+                best = min(best, e0.elapsed_time(e1) * 1e-3)
+            out[name] = 2.0 * n ** 3 / best / 1e12
+            del a, b
+    finally:
+        torch.backends.cuda.matmul.allow_tf32 = old
+    return out
+
+
+CLASSES = {0: "gemm", 1: "qr_f64", 2: "jacobi_svd", 3: "lstsq", 4: "misc", 5: "gram_f64",
+           6: "chol_f64", 7: "tc_matvec"}
+
+
+def read_profile(lib, ctypes):
+    prof = {}
+    for cl, name in CLASSES.items():
+        ms, nl, fl, by = ctypes.c_double(), ctypes.c_int64(), ctypes.c_double(), ctypes.c_double()
+        lib.tt_profile_read(cl, ctypes.byref(ms), ctypes.byref(nl), ctypes.byref(fl), ctypes.byref(by))
+        prof[name] = dict(ms=ms.value, launches=nl.value, flops=fl.value, bytes=by.value)
+    return prof
+
+
+def timed_solves(torch, g, op, b, kw, ws, steps, flush, stream):
+    times, infos = [], []
+    for _ in range(steps):
+        flush.fill_(1)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        x, info = g.tt_sgmres_solve(op, b, workspace=ws, **kw)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1) * 1e-3)
+        infos.append(info)
+    return times, infos, x
+
+
+def extra_configs(torch, g, flush, stream, modes):
+    """The other configurations' solves (not part of the headline): the FP64
+    Laplacian (d = 4, n = 16), the large-rank Laplacian (d = 20, n = 128, rank
+    cap 128) in the mixed mode and in FP64, and one forward + adjoint solve of
+    the differentiable workload (d = 12, n = 64)."""
+    out = {}
+
+    def solve_cfg(name, mode, reps):
+        w = ti.workload(name)
+        p = w.params
+        op = g.op_to_device(w.op)
+        b = g.TT.from_numpy(w.b)
+        kw = dict(maxit=p["maxit"], tol=p["tol"], rmax=p["rmax"], mode=mode, s=p["s"],
+                  round_tol=p.get("round_tol", 0.0), eta=p.get("eta", 0.1),
+                  stop_safety=0.01 if name == "laplace_fp64" else 0.1, r_sol=p["r_sol"],
+                  oversample=p["oversample"], seed=0, max_restarts=8)
+        x, info = g.tt_sgmres_solve(op, b, **kw)  # warm (allocates the workspace)
+        ws = torch.empty(info["workspace_bytes"], dtype=torch.uint8, device="cuda")
+        t, infos, _ = timed_solves(torch, g, op, b, kw, ws, reps, flush, stream)
+        del ws
+        torch.cuda.empty_cache()
+        inf = infos[-1]
+        return {"seconds": statistics.median(t), "iters": inf["iters"], "cycles": inf["cycles"],
+                "true_res": inf["true_res"], "max_rank": inf["max_rank"], "runs": reps}
+
+    out["laplace_fp64_d4_n16"] = {"fp64": solve_cfg("laplace_fp64", g.MODE_FP64, 3)}
+    lr = {}
+    for mname in modes:
+        lr[mname] = solve_cfg("large_rank", {"tf32": g.MODE_TF32, "fp32": g.MODE_FP32,
+                                             "fp64": g.MODE_FP64}[mname], 2)
+    if "fp64" in lr:
+        for mname in lr:
+            if mname != "fp64":
+                lr[mname]["speedup_vs_fp64_gpu"] = lr["fp64"]["seconds"] / lr[mname]["seconds"]
+    out["large_rank_d20_n128"] = lr
+    # differentiable workload: forward solve + adjoint solve + backward contractions
+    w = ti.workload("differentiable")
+    p = w.params
+    theta = torch.tensor(w.extra["theta"], dtype=torch.float64, device="cuda", requires_grad=True)
+    M = torch.as_tensor(w.extra["L"], device="cuda")
+    bc = [torch.as_tensor(c, device="cuda").requires_grad_(True) for c in w.b]
+    xt = [torch.as_tensor(c, device="cuda") for c in w.extra["x_target"]]
+    kw = dict(maxit=p["maxit"], tol=1e-8, rmax=p["rmax"], mode=g.MODE_FP32, r_sol=p["r_sol"],
+              oversample=p["oversample"], seed=0, max_restarts=10)
+    for rep in range(2):
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        loss = g.solve_loss(theta, M, bc, xt, **kw)
+        loss.backward()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        theta.grad = None
+        for c in bc:
+            c.grad = None
+    last = g.solve_loss.last
+    out["differentiable_d12_n64"] = {
+        "fp32_forward_plus_adjoint_seconds": e0.elapsed_time(e1) * 1e-3,
+        "forward_iters": last["last_info"]["iters"],
+        "adjoint_iters": last["last_adjoint_info"]["iters"],
+        "forward_true_res": last["last_info"]["true_res"],
+        "adjoint_true_res": last["last_adjoint_info"]["true_res"]}
+    return out
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -236,123 +388,98 @@ def run_ours(args):
         if world > 1:
             dist.barrier()
 
-    # host oracle sample first (rank 0, single GPU), before any GPU work
+    w, p = workload()
+    # host oracle (rank 0, single GPU), one full solve, before any GPU work
     cpu = None
-    if rank == 0 and world == 1:
-        s_it, its, cores, dt = oracle_sample(args.cpu_seconds, "baseline")
-        cpu = (s_it, its, cores, dt)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = oracle_full_solve(w, p)
 
     mode_name = args.mode or os.environ.get("TTSG_MODE", "tf32")
     mode = {"tf32": g.MODE_TF32, "fp32": g.MODE_FP32, "fp64": g.MODE_FP64}[mode_name]
-    w, p = workload()
     op = g.op_to_device(w.op)
     b = g.TT.from_numpy(w.b)
     kw = dict(maxit=p["maxit"], tol=p["tol"], rmax=p["rmax"], s=p["s"], eta=p["eta"],
               stop_safety=0.1, r_sol=p["r_sol"], oversample=p["oversample"], seed=0,
-              max_restarts=8)
+              max_restarts=8, mode=mode)
     stream = torch.cuda.current_stream()
     flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+    pk, pk_kind = peaks()
+    alu = measured_alu_peaks(torch)
 
-    # warm-up (the last one profiles every kernel class to find the dominant one)
     ws = None
-    info = None
-    for i in range(args.warmup):
-        if i == args.warmup - 1:
-            lib.tt_profile(0xFF)
-        x, info = g.tt_sgmres_solve(op, b, mode=mode, workspace=ws, **kw)
+    for _ in range(args.warmup):
+        x, info = g.tt_sgmres_solve(op, b, workspace=ws, **kw)
         if ws is None:
             ws = torch.empty(info["workspace_bytes"], dtype=torch.uint8, device="cuda")
     torch.cuda.synchronize()
-    classes = {0: "gemm", 1: "qr_f64", 2: "jacobi_svd", 3: "lstsq", 4: "misc", 5: "gram_f64",
-               6: "chol_f64", 7: "tc_matvec"}
-    prof = {}
-    for cl in classes:
-        ms, nl, fl, by = ctypes.c_double(), ctypes.c_int64(), ctypes.c_double(), ctypes.c_double()
-        lib.tt_profile_read(cl, ctypes.byref(ms), ctypes.byref(nl), ctypes.byref(fl), ctypes.byref(by))
-        prof[classes[cl]] = dict(ms=ms.value, launches=nl.value, flops=fl.value, bytes=by.value)
-    dom = max(prof, key=lambda k: prof[k]["ms"])
-    dom_cls = [k for k, v in classes.items() if v == dom][0]
 
-    # timed region: the dominant class is event-timed live
-    lib.tt_profile(1 << dom_cls)
+    # headline: K whole solves, no per-launch profiling
+    lib.tt_profile(0)
     clocks = Clocks(local)
-    times = []
-    iters = []
     launches0 = lib.tt_launch_count()
     barrier()
     torch.cuda.synchronize()
     clocks.start()
-    for _ in range(args.steps):
-        flush.fill_(1)
-        torch.cuda.synchronize()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        x, info = g.tt_sgmres_solve(op, b, mode=mode, workspace=ws, **kw)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        times.append(e0.elapsed_time(e1))
-        iters.append(info["iters"])
+    times, infos, x = timed_solves(torch, g, op, b, kw, ws, args.steps, flush, stream)
     torch.cuda.synchronize()
     barrier()
     clk = clocks.stop()
     launches = lib.tt_launch_count() - launches0
-    total_ms = max_over_ranks(sum(times), "cuda")
-    ms, nl, fl, by = ctypes.c_double(), ctypes.c_int64(), ctypes.c_double(), ctypes.c_double()
-    lib.tt_profile_read(dom_cls, ctypes.byref(ms), ctypes.byref(nl), ctypes.byref(fl), ctypes.byref(by))
-    lib.tt_profile(0)
-    ms_per_step = total_ms / args.steps
-    value = ms_per_step / 1e3
+    total_s = max_over_ranks(sum(times), "cuda")
+    value = total_s / args.steps
+    ms_per_step = value * 1e3
+    info = infos[-1]
+    iters = [i["iters"] for i in infos]
 
-    pk, pk_kind = peaks()
-    avg_ms = ms.value / max(nl.value, 1)
-    fl_per = fl.value / max(nl.value, 1)
-    by_per = by.value / max(nl.value, 1)
+    # roofline: a separate pass of the same solves with every launch of every
+    # kernel class bracketed by CUDA events on the solver's stream
+    nprof = max(2, min(5, args.steps))
+    lib.tt_profile(0xFF)
+    ptimes, _, _ = timed_solves(torch, g, op, b, kw, ws, nprof, flush, stream)
+    prof = read_profile(lib, ctypes)
+    lib.tt_profile(0)
+    prof_total_ms = sum(ptimes) * 1e3
+    dom = max(prof, key=lambda k: prof[k]["ms"])
+    v = prof[dom]
+    avg_ms = v["ms"] / max(v["launches"], 1)
+    fl_per = v["flops"] / max(v["launches"], 1)
+    by_per = v["bytes"] / max(v["launches"], 1)
     if dom == "qr_f64":
-        roof = {"bound": "alu", "achieved": fl_per / (avg_ms * 1e-3) / 1e12,
-                "peak": FP64_ALU_TFLOPS, "unit": "TFLOP/s",
-                "peak_kind": "FP64 CUDA-core peak from unit counts (152 SMs x 2 DFMA/clk x 2.07 GHz)"}
+        roof = {"bound": "alu", "achieved": fl_per / (avg_ms * 1e-3) / 1e12, "peak": alu["fp64"],
+                "unit": "TFLOP/s", "peak_kind": "measured cuBLAS FP64 GEMM on this GPU",
+                "flops_per_launch": fl_per,
+                "flop_count": "2 m l^2 per m x l factorisation (the FP64 QR count 2 n l^3 with "
+                              "m = n l)"}
     elif dom == "gemm":
-        if mode == g.MODE_TF32:
-            peak_c = pk["bf16_tflops_sustained"] * TF32_OVER_BF16
-            kind = f"{pk_kind} BF16 sustained x 1.1/2.25 (TF32)"
-            bound = "tensor"
-        elif mode == g.MODE_FP32:
-            peak_c, kind, bound = FP32_ALU_TFLOPS, "FP32 CUDA-core peak from unit counts", "alu"
-        else:
-            peak_c, kind, bound = FP64_ALU_TFLOPS, "FP64 CUDA-core peak from unit counts", "alu"
+        peak_c = alu["fp64"] if mode == g.MODE_FP64 else alu["fp32"]
         ai = fl_per / max(by_per, 1)
         if ai < peak_c * 1e12 / (pk["hbm_gbs"] * 1e9):
             roof = {"bound": "hbm", "achieved": by_per / (avg_ms * 1e-3) / 1e9,
                     "peak": pk["hbm_gbs"], "unit": "GB/s", "peak_kind": f"{pk_kind} copy bandwidth"}
         else:
-            roof = {"bound": bound, "achieved": fl_per / (avg_ms * 1e-3) / 1e12, "peak": peak_c,
-                    "unit": "TFLOP/s", "peak_kind": kind}
+            roof = {"bound": "alu", "achieved": fl_per / (avg_ms * 1e-3) / 1e12, "peak": peak_c,
+                    "unit": "TFLOP/s", "peak_kind": "measured cuBLAS GEMM (no TF32) on this GPU"}
     else:
         roof = {"bound": "hbm", "achieved": by_per / (avg_ms * 1e-3) / 1e9, "peak": pk["hbm_gbs"],
                 "unit": "GB/s", "peak_kind": f"{pk_kind} copy bandwidth"}
     roof["frac"] = roof["achieved"] / roof["peak"]
     roof["traffic"] = TRAFFIC_BYTES.get(dom)
     roof["kernel"] = dom
-    roof["launches_per_step"] = nl.value / args.steps
+    roof["launches_per_step"] = v["launches"] / nprof
     roof["avg_launch_us"] = avg_ms * 1e3
-    roof["share_of_step"] = ms.value / total_ms if total_ms > 0 else None
+    roof["share_of_step"] = v["ms"] / prof_total_ms if prof_total_ms > 0 else None
+    roof["timed_over"] = f"{nprof} event-profiled solves after the headline loop"
 
-    # FP64 GPU leg (the "mixed vs FP64 GPU" comparison): one solve
+    # FP64 GPU leg (the "mixed vs FP64 GPU" comparison)
     fp64 = None
     if not args.no_fp64_leg and mode != g.MODE_FP64:
-        xf, inf64 = g.tt_sgmres_solve(op, b, mode=g.MODE_FP64, **kw)
-        torch.cuda.synchronize()
-        flush.fill_(1)
-        torch.cuda.synchronize()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        xf, inf64 = g.tt_sgmres_solve(op, b, mode=g.MODE_FP64, **kw)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        fp64 = dict(seconds=e0.elapsed_time(e1) / 1e3, iters=inf64["iters"],
-                    true_res=inf64["true_res"], cycles=inf64["cycles"])
+        kw64 = dict(kw, mode=g.MODE_FP64)
+        xf, inf64 = g.tt_sgmres_solve(op, b, **kw64)
+        ws64 = torch.empty(inf64["workspace_bytes"], dtype=torch.uint8, device="cuda")
+        t64, i64, _ = timed_solves(torch, g, op, b, kw64, ws64, 2, flush, stream)
+        fp64 = dict(seconds=statistics.median(t64), iters=i64[-1]["iters"],
+                    true_res=i64[-1]["true_res"], cycles=i64[-1]["cycles"], runs=2)
+        del ws64
 
     # end to end: pinned host inputs in, solution out, inside the timed interval
     op_h = [c.cpu().pin_memory() for c in op]
@@ -360,7 +487,7 @@ def run_ours(args):
     op_d = [torch.empty_like(c) for c in op]
     b_d = [torch.empty_like(c) for c in b.cores]
     h2d = sum(c.numel() * c.element_size() for c in op_h + b_h)
-    e2e_ms, d2h = [], 0
+    e2e_s, d2h = [], 0
     for _ in range(args.steps):
         flush.fill_(1)
         torch.cuda.synchronize()
@@ -369,28 +496,33 @@ def run_ours(args):
         e0.record(stream)
         for hsrc, ddst in zip(op_h + b_h, op_d + b_d):
             ddst.copy_(hsrc, non_blocking=True)
-        xe, ie = g.tt_sgmres_solve(op_d, g.TT(b_d), mode=mode, workspace=ws, **kw)
+        xe, ie = g.tt_sgmres_solve(op_d, g.TT(b_d), workspace=ws, **kw)
         outs = [c.to("cpu", non_blocking=True) for c in xe.cores]
-        res_h = torch.tensor([ie["true_res"]])
         e1.record(stream)
         torch.cuda.synchronize()
-        e2e_ms.append(e0.elapsed_time(e1))
+        e2e_s.append(e0.elapsed_time(e1) * 1e-3)
         d2h = sum(o.numel() * o.element_size() for o in outs)
+    e2e_value = max_over_ranks(sum(e2e_s), "cuda") / args.steps
 
-    # the contraction half of the metric: algorithmic TFLOP/s of the tcgen05
-    # matvec (against the TF32 tensor peak; the split-TF32 scheme issues three
-    # products per algorithmic one) and of the CUDA-core GEMMs (against the FP32
-    # unit peak), from the profiled warm-up step
+    # the contraction half of the metric, from the profiled pass: algorithmic
+    # TFLOP/s of the tcgen05 matvec (against the TF32 tensor peak; split TF32
+    # issues three products per algorithmic one) and of the CUDA-core GEMMs
     contraction = {}
     for key, peak_c, kind in (("tc_matvec", pk["bf16_tflops_sustained"] * TF32_OVER_BF16,
                                f"{pk_kind} BF16 sustained x 1.1/2.25 (TF32 tensor)"),
-                              ("gemm", FP32_ALU_TFLOPS, "FP32 CUDA-core peak from unit counts")):
-        v = prof[key]
-        if v["ms"] > 0 and v["launches"] > 0:
-            tf = v["flops"] / (v["ms"] * 1e-3) / 1e12
+                              ("gemm", alu["fp32"], "measured cuBLAS FP32 GEMM (no TF32)")):
+        vv = prof[key]
+        if vv["ms"] > 0 and vv["launches"] > 0:
+            tf = vv["flops"] / (vv["ms"] * 1e-3) / 1e12
             contraction[key] = {"tflops": tf, "peak": peak_c, "frac": tf / peak_c,
-                                "peak_kind": kind, "launches": v["launches"],
-                                "avg_launch_us": v["ms"] * 1e3 / v["launches"]}
+                                "peak_kind": kind, "launches": vv["launches"],
+                                "avg_launch_us": vv["ms"] * 1e3 / vv["launches"]}
+    extras = None
+    if not args.no_extras and world == 1:
+        del ws
+        torch.cuda.empty_cache()
+        extras = extra_configs(torch, g, flush, stream,
+                               [m for m in (mode_name, "fp64")])
     line = {"metric": METRIC, "value": value, "unit": "s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None,
@@ -400,24 +532,27 @@ def run_ours(args):
                        "l2": "flushed (512 MiB write) before every step"},
             "iters_per_solve": statistics.median(iters), "true_res": info["true_res"],
             "svd_nonconverged": info.get("svd_nonconverged"),
-            "svd_sweeps": {"max": info.get("svd_max_sweeps"),
-                           "mean": round(info.get("svd_mean_sweeps") or 0.0, 2)},
             "cycles": info["cycles"], "max_rank": info["max_rank"],
             "gpu_launches": int(launches), "roofline": roof, "contraction": contraction,
-            "kernel_time_ms_by_class_warmup": {k: round(v["ms"], 3) for k, v in prof.items()},
-            "e2e": {"value": statistics.mean(e2e_ms) / 1e3, "unit": "s", "h2d_bytes_per_step": h2d,
+            "measured_peaks_tflops": alu,
+            "kernel_time_ms_by_class_profiled": {k: round(vv["ms"] / nprof, 3)
+                                                 for k, vv in prof.items()},
+            "e2e": {"value": e2e_value, "unit": "s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
             "clocks": clk}
     if fp64:
         line["fp64_gpu"] = fp64
         line["speedup_vs_fp64_gpu"] = fp64["seconds"] / value
     if cpu is not None:
-        s_it, its, cores, dt = cpu
-        proj = s_it * statistics.median(iters)
-        line["cpu_baseline"] = {"value": proj, "unit": "s", "cores": cores, "kind": "oracle",
-                                "sample": f"{its} Krylov iterations of the FP64 oracle's first "
-                                          f"cycle ({dt:.1f} s), projected to the GPU solve's "
-                                          f"{statistics.median(iters)} iterations"}
+        dt, cinfo = cpu
+        line["cpu_baseline"] = {"value": dt, "unit": "s", "cores": host_cores(), "kind": "oracle",
+                                "sample": f"1 full FP64 oracle solve ({cinfo['iters']} iterations, "
+                                          f"{len(cinfo['cycles'])} cycle(s), true residual "
+                                          f"{cinfo['true_res']:.2e}; restarts, final rounding and "
+                                          f"exact residual included)"}
+        line["speedup_vs_cpu_oracle"] = dt / value
+    if extras:
+        line["other_configs"] = extras
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
