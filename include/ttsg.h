@@ -36,6 +36,14 @@
  * Errors.  Every function returns TT_OK (0) or a TT_ERR_* code; tt_last_error()
  *   returns a message for the calling thread's last failure.  Argument errors
  *   are detected on the host before any launch.
+ * Devices.  Kernel attributes and the SM count are set up once per process, on
+ *   the device of the first call; use one device per process.
+ * Memory model.  The library never allocates device memory for its outputs or
+ *   scratch: every call takes caller-owned buffers, sized by the *_workspace
+ *   queries and by the capacities of tt_vec_out.  There is therefore no
+ *   library context, allocator callback or free function, and no out-of-memory
+ *   status (a workspace below the query's answer gives TT_ERR_WORKSPACE); the
+ *   element type of every buffer follows from ``mode``.
  */
 #ifndef TTSG_H
 #define TTSG_H
@@ -54,6 +62,9 @@ extern "C" {
 #define TT_ERR_TIMEOUT 4       /* a bounded device-side wait expired */
 #define TT_ERR_NOT_CONVERGED 5 /* solver stopped at maxit / restarts; x is returned */
 #define TT_ERR_UNSUPPORTED 6   /* mode or size the library does not support */
+#define TT_ERR_BREAKDOWN 7     /* solver: h_{k+1,k} = 0 (the Krylov space became invariant
+                                  under A) in a cycle and the true residual stayed above tol;
+                                  x is returned (exact in that space) */
 
 #define TT_MODE_FP64 0
 #define TT_MODE_FP32 1
@@ -117,6 +128,19 @@ int tt_sketch(int mode, const tt_vec* x, int64_t s, void* const* S, double* out,
 size_t tt_sketch_workspace(int mode, const tt_vec* x, int64_t s);
 
 /*
+ * tt_sketch_factors - the Khatri-Rao factors S_k of the solver's sketch
+ * (Sec. 3.1; Alg. 4's input S): S[k] (device, [s][n_k], double for
+ * TT_MODE_FP64, float otherwise) receives i.i.d. N(0, s^(-1/d)) entries, factor k
+ * being element 0..s*n_k-1 of the Gaussian stream (seed, 1024 + k) of
+ * tt_gaussian.  The variance s^(-1/d) makes E ||S_odot x||^2 = ||x||^2.
+ * tt_sgmres_solve draws exactly these factors from its ``seed``.
+ * n: host array [d].  Errors: TT_ERR_ARG for d outside 1..TT_MAX_D, s < 1,
+ * n[k] < 1 or null pointers.
+ */
+int tt_sketch_factors(int mode, int d, const int64_t* n, int64_t s, uint64_t seed, void* const* S,
+                      void* stream);
+
+/*
  * tt_dot - <x, y> by the left-to-right Gram sweep (used for h_{k,k} = w^T v_k
  * and the norms of Alg. 4).  out (device, double[1]).
  */
@@ -134,9 +158,16 @@ size_t tt_dot_workspace(int mode, const tt_vec* x, const tt_vec* y);
  * that loads the library keeps until the process exits.  Inputs that would
  * need more scratch than that are rejected with TT_ERR_ARG before any device
  * work.  The first call on a device looks up the array's device address; make
- * that first call before any stream capture.  All calls share the one array, so
- * calls that overlap on the GPU (different streams, or threads, at the same
- * time) race; serialise them.  The function calls no cudaMalloc or cudaFree.
+ * that first call before any stream capture, and at start-up, before a memory
+ * manager takes the device's memory: with lazy module loading the array itself
+ * is created at that first look-up.  The looked-up address is cached per device
+ * index for the life of the process; after a cudaDeviceReset the cache is
+ * stale, so do not call this function after resetting a device.  All calls
+ * share the one array, so calls that overlap on the GPU (different streams, or
+ * threads, at the same time) race; serialise them.  The function calls no
+ * cudaMalloc or cudaFree.  Errors: the status of the size query for bad
+ * arguments (TT_ERR_ARG, TT_ERR_UNSUPPORTED), TT_ERR_ARG for inputs beyond the
+ * fixed array, TT_ERR_CUDA if the look-up fails.
  * out (device, double[1]); x, y as for tt_dot.
  */
 #define TT_NOALLOC_SCRATCH_BYTES (16u << 20)
@@ -299,7 +330,7 @@ typedef struct {
   double sketched_res;  /* last sketched relative residual */
   double true_res;      /* final true relative residual (FP64, exact TT) */
   int64_t max_rank;     /* largest basis rank seen */
-  int status;           /* TT_OK or TT_ERR_NOT_CONVERGED */
+  int status;           /* TT_OK, TT_ERR_NOT_CONVERGED or TT_ERR_BREAKDOWN */
   double seconds;       /* host wall time of the call */
   double* res_hist;     /* optional host array [hist_cap]: sketched residuals */
   int64_t* rank_hist;   /* optional host array [hist_cap]: basis max ranks */
@@ -307,6 +338,7 @@ typedef struct {
   int svd_nonconverged; /* small SVDs that reached their sweep cap (diagnostic) */
   int svd_max_sweeps;   /* most Jacobi sweeps any small SVD took (diagnostic) */
   double svd_mean_sweeps; /* mean Jacobi sweeps per small SVD (diagnostic) */
+  int breakdowns;       /* cycles that ended on h_{k+1,k} = 0 */
 } tt_solver_info;
 
 /*

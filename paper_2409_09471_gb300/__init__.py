@@ -27,7 +27,7 @@ import torch
 from ._abi import (lib, TTVec, TTVecOut, TTOp, TTPrecond, SolverParams, SolverInfo, MODE_FP64,
                    MODE_FP32, MODE_TF32, TTError, check, LIB_PATH)
 
-__all__ = ["TT", "tt_matvec", "tt_sketch", "tt_dot", "tt_round_rand", "tt_gaussian", "tt_qr_f64",
+__all__ = ["TT", "tt_matvec", "tt_sketch", "tt_sketch_factors", "tt_dot", "tt_round_rand", "tt_gaussian", "tt_qr_f64",
            "tt_lstsq_f64", "tt_sgmres_solve", "MODE_FP64", "MODE_FP32", "MODE_TF32", "TTError",
            "LIB_PATH", "mode_dtype", "op_to_device", "tt_dot_grad", "tt_local_dots",
            "tt_kron_sum_op", "tt_op_transpose", "solve_loss", "tt_qr_f64_batched",
@@ -133,6 +133,19 @@ def tt_sketch(x: TT, S: Sequence[torch.Tensor], mode: int = MODE_FP64, stream=No
     check(lib.tt_sketch(mode, ctypes.byref(xd), s, Sp, ctypes.c_void_p(out.data_ptr()),
                         ctypes.c_void_p(ws.data_ptr()), ws.numel(), _stream(stream)))
     return out
+
+
+def tt_sketch_factors(ns: Sequence[int], s: int, seed: int = 0, mode: int = MODE_FP64,
+                      device="cuda", stream=None) -> List[torch.Tensor]:
+    """The Khatri-Rao factors ``S_k`` (``[s, n_k]``, entries N(0, s^(-1/d)))
+    that :func:`tt_sgmres_solve` draws from ``seed``."""
+    d = len(ns)
+    S = [torch.empty((s, n), dtype=mode_dtype(mode), device=device) for n in ns]
+    n_arr = (ctypes.c_int64 * d)(*ns)
+    sp = (ctypes.c_void_p * d)(*[t.data_ptr() for t in S])
+    check(lib.tt_sketch_factors(mode, d, n_arr, int(s), ctypes.c_uint64(seed), sp,
+                                _stream(stream)))
+    return S
 
 
 def tt_dot(x: TT, y: TT, mode: int = MODE_FP64, stream=None) -> torch.Tensor:
@@ -285,7 +298,7 @@ def tt_sgmres_solve(op, b: TT, maxit: int, tol: float, rmax: int, mode: int = MO
                                  ctypes.byref(xd), ctypes.byref(info),
                                  ctypes.c_void_p(workspace.data_ptr()), workspace.numel(),
                                  _stream(stream))
-    if rc not in (0, 5) or (rc == 5 and raise_on_nonconvergence):
+    if rc not in (0, 5, 7) or (rc in (5, 7) and raise_on_nonconvergence):
         check(rc)
     r = list(rank_arr)
     x = TT([xc[k][: r[k] * b.ns[k] * r[k + 1]].view(r[k], b.ns[k], r[k + 1]) for k in range(d)])
@@ -294,7 +307,7 @@ def tt_sgmres_solve(op, b: TT, maxit: int, tol: float, rmax: int, mode: int = MO
                true_res=info.true_res, max_rank=info.max_rank, status=info.status,
                seconds=info.seconds, res_hist=list(rh[:n]), rank_hist=list(kh[:n]),
                svd_nonconverged=info.svd_nonconverged, svd_max_sweeps=info.svd_max_sweeps,
-               svd_mean_sweeps=info.svd_mean_sweeps,
+               svd_mean_sweeps=info.svd_mean_sweeps, breakdowns=info.breakdowns,
                workspace_bytes=int(need))
     return x, out
 
@@ -659,7 +672,7 @@ def tt_sgmres_solve_batched(op, bs: Sequence[TT], maxit: int, tol: float, rmax: 
     rc = lib.tt_sgmres_solve_batched(ctypes.byref(od), nrhs, barr, ctypes.byref(p), xarr, infos,
                                      int(nworkers), ctypes.c_void_p(workspace.data_ptr()),
                                      workspace.numel())
-    if rc not in (0, 5):
+    if rc not in (0, 5, 7):
         check(rc)
     res = []
     for i, b in enumerate(bs):
@@ -670,5 +683,5 @@ def tt_sgmres_solve_batched(op, bs: Sequence[TT], maxit: int, tol: float, rmax: 
         res.append((x, dict(iters=inf.iters, cycles=inf.cycles, sketched_res=inf.sketched_res,
                             true_res=inf.true_res, max_rank=inf.max_rank, status=inf.status,
                             seconds=inf.seconds, svd_nonconverged=inf.svd_nonconverged,
-                            workspace_bytes=int(need))))
+                            breakdowns=inf.breakdowns, workspace_bytes=int(need))))
     return res

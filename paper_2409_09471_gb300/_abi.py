@@ -10,7 +10,8 @@ LIB_PATH = os.path.join(HERE, "libttsg.so")
 
 MODE_FP64, MODE_FP32, MODE_TF32 = 0, 1, 2
 STATUS = {0: "TT_OK", 1: "TT_ERR_ARG", 2: "TT_ERR_WORKSPACE", 3: "TT_ERR_CUDA",
-          4: "TT_ERR_TIMEOUT", 5: "TT_ERR_NOT_CONVERGED", 6: "TT_ERR_UNSUPPORTED"}
+          4: "TT_ERR_TIMEOUT", 5: "TT_ERR_NOT_CONVERGED", 6: "TT_ERR_UNSUPPORTED",
+          7: "TT_ERR_BREAKDOWN"}
 
 c_i64p = ctypes.POINTER(ctypes.c_int64)
 c_vpp = ctypes.POINTER(ctypes.c_void_p)
@@ -50,7 +51,7 @@ class SolverInfo(ctypes.Structure):
                 ("seconds", ctypes.c_double), ("res_hist", ctypes.POINTER(ctypes.c_double)),
                 ("rank_hist", ctypes.POINTER(ctypes.c_int64)), ("hist_cap", ctypes.c_int),
                 ("svd_nonconverged", ctypes.c_int), ("svd_max_sweeps", ctypes.c_int),
-                ("svd_mean_sweeps", ctypes.c_double)]
+                ("svd_mean_sweeps", ctypes.c_double), ("breakdowns", ctypes.c_int)]
 
 
 class TTError(RuntimeError):
@@ -75,6 +76,7 @@ def _load():
         "tt_sketch": (cint, [cint, P(TTVec), i64, c_vpp, V, V, sz, V]),
         "tt_sketch_workspace": (sz, [cint, P(TTVec), i64]),
         "tt_dot": (cint, [cint, P(TTVec), P(TTVec), V, V, sz, V]),
+        "tt_sketch_factors": (cint, [cint, cint, c_i64p, i64, u64, c_vpp, V]),
         "tt_dot_workspace": (sz, [cint, P(TTVec), P(TTVec)]),
         "tt_dot_noalloc": (cint, [cint, P(TTVec), P(TTVec), V, V]),
         "tt_round_rand": (cint, [cint, cint, P(TTVec), P(dbl), dbl, i64, i64, u64, c_vpp, c_i64p,

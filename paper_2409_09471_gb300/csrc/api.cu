@@ -158,6 +158,9 @@ void do_matvec(int mode, const tt_op* A, const tt_vec* x, const tt_vec* y, void*
   if (dry) throw (size_t)cv.ar.peak;
 }
 
+// status of the last workspace query that failed (0 queries return 0 bytes)
+thread_local int g_measure_code = TT_OK;
+
 template <typename F>
 size_t measure(F&& f, bool margin = true) {
   DryGuard g;
@@ -165,11 +168,14 @@ size_t measure(F&& f, bool margin = true) {
     f();
   } catch (size_t peak) {
     // margin for allocations whose size the dry run bounds from below
+    g_measure_code = TT_OK;
     return margin ? peak + peak / 32 + (16u << 20) : peak;
   } catch (const Error& e) {
     g_last_error = e.what();
+    g_measure_code = e.code;
     return 0;
   }
+  g_measure_code = TT_ERR_ARG;
   return 0;
 }
 
@@ -326,14 +332,16 @@ int tt_dot(int mode, const tt_vec* x, const tt_vec* y, double* out, void* ws, si
 namespace ttsg {
 // Inner product without split-K scratch, on a caller-chosen workspace; used by
 // the allocation-free entry point (noalloc.cu).
-size_t dot_bytes_without_splitk(int mode, const tt_vec* x, const tt_vec* y) {
-  return measure([&] {
+size_t dot_bytes_without_splitk(int mode, const tt_vec* x, const tt_vec* y, int* code) {
+  const size_t need = measure([&] {
     check_mode(mode);
     if (mode == TT_MODE_FP64)
       do_dot<double>(mode, x, y, nullptr, nullptr, 0, nullptr, true, false);
     else
       do_dot<float>(mode, x, y, nullptr, nullptr, 0, nullptr, true, false);
   }, false);
+  if (code) *code = need ? TT_OK : g_measure_code;
+  return need;
 }
 int dot_on_workspace_without_splitk(int mode, const tt_vec* x, const tt_vec* y, double* out,
                                     void* ws, size_t bytes, void* stream) {
@@ -464,6 +472,20 @@ int tt_stta_recover(int d, const int64_t* n, const int64_t* r, const int64_t* l,
                     double* const* cores, void* ws, size_t ws_bytes, void* stream) {
   return guarded([&] {
     do_stta_recover(d, n, r, l, psi, omega, rcond, cores, ws, ws_bytes, stream, false);
+  });
+}
+
+int tt_sketch_factors(int mode, int d, const int64_t* n, int64_t s, uint64_t seed,
+                      void* const* S, void* stream) {
+  return guarded([&] {
+    check_mode(mode);
+    if (d < 1 || d > MAXD || !n || !S || s < 1) throw Error(TT_ERR_ARG, "sketch_factors: arguments");
+    for (int k = 0; k < d; ++k) {
+      if (n[k] < 1 || !S[k]) throw Error(TT_ERR_ARG, "sketch_factors: n[k] >= 1, S[k] non-null");
+      // variance s^(-1/d): E ||S_odot x||^2 = ||x||^2 (Sec. 3.1)
+      gaussian_fill(S[k], mode == TT_MODE_FP64, s * n[k], seed, 1024 + (uint64_t)k,
+                    std::pow((double)s, -0.5 / d), (cudaStream_t)stream);
+    }
   });
 }
 
@@ -691,15 +713,16 @@ void do_solve(const tt_op* A, const tt_vec* b, const tt_solver_params* p, const 
     info->svd_nonconverged = r.svd_nonconverged;
     info->svd_max_sweeps = r.svd_max_sweeps;
     info->svd_mean_sweeps = r.svd_mean_sweeps;
+    info->breakdowns = r.breakdowns;
     for (int i = 0; i < info->hist_cap && i < (int)r.res_hist.size(); ++i) {
       if (info->res_hist) info->res_hist[i] = r.res_hist[i];
       if (info->rank_hist) info->rank_hist[i] = r.rank_hist[i];
     }
   }
   if (r.status != TT_OK)
-    throw Error(TT_ERR_NOT_CONVERGED, "solve: true residual " + std::to_string(r.true_res) +
-                                          " above tol after " + std::to_string(r.cycles) +
-                                          " cycles");
+    throw Error(r.status, "solve: true residual " + std::to_string(r.true_res) + " above tol after " +
+                              std::to_string(r.cycles) + " cycles" +
+                              (r.breakdowns ? " (the Krylov space became invariant)" : ""));
 }
 }  // namespace
 
@@ -909,7 +932,7 @@ int tt_sgmres_solve_batched(const tt_op* A, int nrhs, const tt_vec* b, const tt_
           const int rc = guarded([&] {
             do_solve(A, &b[i], p, &x[i], info ? &info[i] : nullptr, slice, per, st, false);
           });
-          if (rc == TT_ERR_NOT_CONVERGED) {
+          if (rc == TT_ERR_NOT_CONVERGED || rc == TT_ERR_BREAKDOWN) {
             std::lock_guard<std::mutex> lk(mu);
             ++not_conv;
           } else if (rc != TT_OK) {

@@ -10,7 +10,7 @@
 #include <mutex>
 
 namespace ttsg {
-size_t dot_bytes_without_splitk(int mode, const tt_vec* x, const tt_vec* y);
+size_t dot_bytes_without_splitk(int mode, const tt_vec* x, const tt_vec* y, int* code);
 int dot_on_workspace_without_splitk(int mode, const tt_vec* x, const tt_vec* y, double* out,
                                     void* ws, size_t bytes, void* stream);
 }  // namespace ttsg
@@ -51,8 +51,9 @@ int noalloc_scratch(void** ptr) {
 
 int tt_dot_noalloc(int mode, const tt_vec* x, const tt_vec* y, double* out, void* stream) {
   // size check on the host before touching the device
-  const size_t need = ttsg::dot_bytes_without_splitk(mode, x, y);
-  if (need == 0) return TT_ERR_ARG;  // argument error; message already set
+  int code = TT_OK;
+  const size_t need = ttsg::dot_bytes_without_splitk(mode, x, y, &code);
+  if (need == 0) return code;  // the query's own status; message already set
   if (need > (size_t)TT_NOALLOC_SCRATCH_BYTES) {
     ttsg::set_last_error("tt_dot_noalloc: these ranks need " + std::to_string(need) +
                          " bytes of scratch, more than the fixed " +

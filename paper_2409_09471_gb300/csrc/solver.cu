@@ -390,18 +390,32 @@ SolveResult sgmres_solve(const Ctx& c0, const TTop<double>& A64in, const TTv<dou
         copy3d({sg}, c.st);
       }
       lstsq_add_column(Wm, Sr0, s, k, p.maxit, lsws, ydev, scal + 4, c.st);
-      double hv[2] = {1.0, 1.0};
+      // scal[1..4]: h_{k,k}, ||v~||^2, ||v~|| = h_{k+1,k}, sketched residual
+      double hs4[4] = {0.0, 1.0, 1.0, 1.0};
       if (!g_dry_run) {
-        TT_CUDA(cudaMemcpyAsync(hv, scal + 3, 2 * sizeof(double), cudaMemcpyDeviceToHost, c.st));
+        TT_CUDA(cudaMemcpyAsync(hs4, scal + 1, 4 * sizeof(double), cudaMemcpyDeviceToHost, c.st));
         TT_CUDA(cudaStreamSynchronize(c.st));
       }
+      const double hv[2] = {hs4[2], hs4[3]};
       sres = betaS > 0 ? hv[1] / betaS : 0.0;
       res.res_hist.push_back(sres);
       res.rank_hist.push_back(V[k + 1].max_rank());
       res.max_rank = std::max(res.max_rank, V[k + 1].max_rank());
       kdone = k + 1;
       ++res.iters;
-      if (hv[1] <= inner * betaS || hv[0] == 0.0) break;
+      // h_{k+1,k} = 0 to working precision: ||v~|| at the rounding level of
+      // ||w|| = sqrt(h_{k,k}^2 + h_{k+1,k}^2) (the d core contractions of A v_k
+      // and its rounding each contribute a few units of roundoff).  The Krylov
+      // space is then invariant under A, so the least-squares solution of this
+      // cycle is exact in it (a breakdown), and the new direction would be
+      // rounding noise.
+      const double u_work = f64 ? 0x1p-53 : 0x1p-24;
+      const double wn = std::sqrt(hs4[0] * hs4[0] + hv[0] * hv[0]);
+      if (hv[0] <= 16.0 * d * u_work * wn) {
+        ++res.breakdowns;
+        break;
+      }
+      if (hv[1] <= inner * betaS) break;
       // stagnation: less than 10% progress over the last 10 iterations ends the
       // cycle (the restart continues from the true residual)
       const size_t nh = res.res_hist.size();
@@ -485,7 +499,8 @@ SolveResult sgmres_solve(const Ctx& c0, const TTop<double>& A64in, const TTv<dou
     res.svd_max_sweeps = flags[3];
     res.svd_mean_sweeps = flags[5] > 0 ? (double)flags[4] / flags[5] : 0.0;
   }
-  res.status = res.true_res <= p.tol ? TT_OK : TT_ERR_NOT_CONVERGED;
+  res.status = res.true_res <= p.tol ? TT_OK
+               : (res.breakdowns > 0 ? TT_ERR_BREAKDOWN : TT_ERR_NOT_CONVERGED);
   res.seconds =
       std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
   return res;

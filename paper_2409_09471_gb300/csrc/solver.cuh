@@ -23,6 +23,7 @@ struct SolveParams {
 
 struct SolveResult {
   int iters = 0, cycles = 0, status = TT_OK, svd_nonconverged = 0, svd_max_sweeps = 0;
+  int breakdowns = 0;  // cycles that ended on h_{k+1,k} = 0 (Krylov space invariant)
   double svd_mean_sweeps = 0.0;
   double sketched_res = 0, true_res = 0, seconds = 0;
   int64_t max_rank = 0;

@@ -95,3 +95,30 @@ def test_batched_workload_rhs_subset(g):
     kappa = (np.sin(n * np.pi / (2 * (n + 1))) / np.sin(np.pi / (2 * (n + 1)))) ** 2
     diff = ott.norm(ott.left_orthogonalize(ott.add([(1.0, x1.numpy()), (-1.0, res[3][0].numpy())])))
     assert diff <= 2 * kappa * p["tol"] * ott.norm(x1.numpy())
+
+
+def test_batched_workload_all_64(g):
+    # the whole batched workload: 64 right-hand sides (d = 8, n = 32, bond
+    # ranks U{1..12}), rank cap 150, TF32 mode, in one batched call.  Every
+    # solution's FP64 residual, computed exactly on the device, is at most 1e-6;
+    # every fourth one is recomputed by the oracle (about 4 s each on the host),
+    # which must agree to 1%.
+    w = ti.workload("batched")
+    p = w.params
+    op = g.op_to_device(w.op)
+    bs = [g.TT.from_numpy(b) for b in w.b]
+    assert len(bs) == 64
+    res = g.tt_sgmres_solve_batched(op, bs, maxit=p["maxit"], tol=p["tol"], rmax=p["rmax"],
+                                    mode=g.MODE_TF32, s=p["s"], round_tol=p["round_tol"],
+                                    r_sol=p["r_sol"], oversample=p["oversample"],
+                                    max_restarts=20, nworkers=16)
+    bad = [(i, info["true_res"], info["cycles"], info["iters"]) for i, (_, info) in enumerate(res)
+           if info["status"] != 0 or info["true_res"] > 1e-6]
+    assert not bad, bad
+    for x, _ in res:
+        assert max(x.ranks) <= p["r_sol"]
+    for i in range(0, 64, 4):
+        x, info = res[i]
+        r = osol.true_residual_norm(w.op, x.numpy(), w.b[i]) / ott.norm(w.b[i])
+        assert r <= 1e-6, (i, r)
+        assert abs(r - info["true_res"]) <= 1e-2 * r + 1e-14, (i, r, info["true_res"])

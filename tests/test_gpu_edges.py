@@ -53,8 +53,9 @@ def test_eigenvector_right_hand_side_one_step(g, mode):
     x, info = g.tt_sgmres_solve(g.op_to_device(op), g.TT.from_numpy(q), maxit=20, tol=1e-6,
                                 rmax=8, mode=mode, s=40, stop_safety=0.01)
     assert info["status"] == 0 and info["cycles"] == 1
-    if mode == 0:
-        assert info["iters"] <= 2
+    # ||A q - h q|| is at the rounding level of h: the first step ends on a
+    # breakdown (the Krylov space {q} is invariant under A)
+    assert info["breakdowns"] == 1 and info["iters"] == 1
     r = osol.true_residual_norm(op, x.numpy(), q)
     err = np.linalg.norm(ott.full(x.numpy()) - ott.full(q) / mu)
     assert err <= 1.01 * r / (d * lam[0]) + 1e-15

@@ -279,3 +279,44 @@ def test_qr_f64_wide_rows_in_global_memory(g, m, l):
     Qf, _ = g.tt_qr_f64(Yd.float())
     Qf = Qf.cpu().double().numpy()
     assert np.max(np.abs(Qf.T @ Qf - np.eye(l))) <= 1e-6 * l
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_sketch_factors_match_oracle_philox(g, mode):
+    # the Khatri-Rao factors the solver draws (Philox streams 1024 + k,
+    # variance s^(-1/d)) against the oracle's independent Philox + Box-Muller
+    ns, s = [16, 5, 64, 9], 100
+    S = g.tt_sketch_factors(ns, s, seed=7, mode=mode)
+    ref = oph.sketch_factors(ns, s, seed=7)
+    for a, b in zip(S, ref):
+        assert a.shape == (s, b.shape[1])
+        tol = 1e-13 if mode == 0 else 1e-6
+        assert np.max(np.abs(a.double().cpu().numpy() - b)) <= tol * np.max(np.abs(b))
+    with pytest.raises(g.TTError):
+        g.tt_sketch_factors(ns, 0, seed=7, mode=mode)
+
+
+@pytest.mark.parametrize("mode", [1, 2])
+@pytest.mark.parametrize("seed", [0, 1])
+def test_round_rand_float_truncation_vs_sequential_tt_svd(g, mode, seed):
+    # T = X + delta Y with X of TT rank 5 and a tail delta ||Y|| = 1e-3 ||X||:
+    # at eps = 1e-2 both the float modes' rule (all bonds from one
+    # left-orthogonal tensor, per-bond eps ||T|| / (d - 1)) and the oracle's
+    # sequential TT-SVD (per-bond eps ||T|| / sqrt(d - 1)) keep rank 5 at every
+    # bond, and each result lies within eps ||T|| of T, so the two lie within
+    # 2 eps ||T|| of each other (plus FP32 rounding, well below 1e-5)
+    ns = [12, 70, 8, 33]
+    X = ti.random_tt(ns, [1, 5, 5, 5, 1], seed=60 + seed)
+    Y = ti.random_tt(ns, [1, 3, 3, 3, 1], seed=70 + seed)
+    delta = 1e-3 * ott.norm(X) / ott.norm(Y)
+    terms = [(1.0, X), (delta, Y)]
+    eps, rmax, p = 1e-2, 20, 4
+    drm = ti.gaussian_drm(ns, [1] + [rmax + p] * 3 + [1], seed=80 + seed)
+    ref = ornd.rto_round(terms, drm, eps=eps, rmax=rmax, oversample=p, truncation="sequential")
+    y = g.tt_round_rand([dev_tt(g, c, mode) for _, c in terms], [a for a, _ in terms], eps, rmax,
+                        p, drm=[torch.as_tensor(c, dtype=torch.float32, device="cuda")
+                                for c in drm], mode=mode)
+    assert y.ranks == ott.ranks(ref) == [1, 5, 5, 5, 1]
+    T = ott.add(terms)
+    assert tt_rel_diff(y.numpy(), T) <= eps + 1e-5
+    assert tt_rel_diff(y.numpy(), ref) <= 2 * eps + 1e-5

@@ -8,6 +8,7 @@ import pytest
 
 import ttinputs as ti
 from oracle import tt, rounding as rnd
+from oracle import tt as ott
 
 
 def unfolding_ranks(full, ns, tol=1e-10):
@@ -144,3 +145,30 @@ def test_simultaneous_truncation_error_bound_and_identity(eps):
 
 def ttm_left(cores):
     return tt.left_orthogonalize(cores)
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_simultaneous_equals_sequential_tt_svd_with_a_spectral_gap(seed):
+    # T = X + delta Y with X of TT rank 4 and delta ||Y|| = 1e-14 ||X||: every
+    # bond spectrum has four singular values of order ||X|| and the rest below
+    # 1e-13 of them.  A tolerance inside that gap makes the truncation rank 4
+    # for both rules (each bond's threshold, eps ||T|| / (d - 1) for the
+    # simultaneous rule and eps ||T|| / sqrt(d - 1) for the sequential TT-SVD,
+    # lies far above the tail and far below the kept values), so the two must
+    # keep the same ranks and the same tensor up to the dropped tail.
+    rng = np.random.default_rng(seed)
+    ns = [5, 6, 4, 7, 5]
+    X = ti.random_tt(ns, [1, 4, 4, 4, 4, 1], seed=10 + seed)
+    Y = ti.random_tt(ns, [1, 3, 3, 3, 3, 1], seed=20 + seed)
+    delta = 1e-14 * ott.norm(X) / ott.norm(Y)
+    T = ott.left_orthogonalize(ott.add([(1.0, X), (delta, Y)]))
+    eps = 1e-8 * float(rng.uniform(0.5, 2.0))
+    a = rnd.truncate_simultaneous(T, eps=eps)
+    b = rnd.tt_svd_round(T, eps=eps)
+    assert ott.ranks(a) == ott.ranks(b) == [1, 4, 4, 4, 4, 1]
+    diff = ott.norm(ott.left_orthogonalize(ott.add([(1.0, a), (-1.0, b)])))
+    assert diff <= 1e-12 * ott.norm(T)
+    # and both are within the tolerance of T itself
+    for c in (a, b):
+        err = ott.norm(ott.left_orthogonalize(ott.add([(1.0, c), (-1.0, T)])))
+        assert err <= eps * ott.norm(T)

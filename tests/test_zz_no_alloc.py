@@ -10,6 +10,7 @@ import pytest
 import torch
 
 import ttinputs as ti
+from oracle import tt as ott
 
 pytestmark = pytest.mark.gpu
 
@@ -34,7 +35,7 @@ def _noalloc(g, x, y, mode):
     return rc, out.item()
 
 
-@pytest.mark.parametrize("mode,tol", [(0, 1e-12), (1, 2e-5)])
+@pytest.mark.parametrize("mode,tol", [(0, 1e-12), (1, 2e-5), (2, 2e-5)])
 def test_noalloc_dot_matches_tt_dot_twice(g, mode, tol):
     ns = [13, 64, 7, 30, 64]
     dt = g.mode_dtype(mode)
@@ -44,10 +45,12 @@ def test_noalloc_dot_matches_tt_dot_twice(g, mode, tol):
         x, y = g.TT.from_numpy(xc, dt), g.TT.from_numpy(yc, dt)
         ref = g.tt_dot(x, y, mode=mode).item()
         scale = np.sqrt(g.tt_dot(x, x, mode=mode).item() * g.tt_dot(y, y, mode=mode).item())
+        exact = ott.dot(x.numpy(), y.numpy())  # the oracle, on the stored values
         for _ in range(2):
             rc, val = _noalloc(g, x, y, mode)
             assert rc == 0
             assert abs(val - ref) <= tol * scale
+            assert abs(val - exact) <= tol * scale
 
 
 def test_noalloc_rejects_inputs_beyond_the_fixed_scratch(g):
