@@ -307,8 +307,9 @@ def timed_solves(torch, g, op, b, kw, ws, steps, flush, stream):
 def extra_configs(torch, g, flush, stream, modes):
     """The other configurations' solves (not part of the headline): the FP64
     Laplacian (d = 4, n = 16), the large-rank Laplacian (d = 20, n = 128, rank
-    cap 128) in the mixed mode and in FP64, and one forward + adjoint solve of
-    the differentiable workload (d = 12, n = 64)."""
+    cap 128) in the mixed mode and in FP64, the preconditioned Markov-chain
+    system (d = 5, n = 128) in FP64 and FP32, and one forward + adjoint
+    solve of the differentiable workload (d = 12, n = 64)."""
     out = {}
 
     def solve_cfg(name, mode, reps):
@@ -339,6 +340,38 @@ def extra_configs(torch, g, flush, stream, modes):
             if mname != "fp64":
                 lr[mname]["speedup_vs_fp64_gpu"] = lr["fp64"]["seconds"] / lr[mname]["seconds"]
     out["large_rank_d20_n128"] = lr
+    # Markov chain (d = 5 coupled random walks of n = 128 states, the paper's
+    # smallest size, at its rank cap 80), right-preconditioned by the
+    # exponential sum of the shifted independent part; the shift is a third of
+    # the smallest spectral gap in FP64 and the whole gap in FP32 (the float
+    # products cannot resolve the 1/sigma amplification of a smaller shift)
+    w = ti.workload("markov", n=128)
+    p = w.params
+    op = g.op_to_device(w.op)
+    b = g.TT.from_numpy(w.b)
+    mk = {}
+    for mname, mval, frac in (("fp64", g.MODE_FP64, 0.3), ("fp32", g.MODE_FP32, 1.0)):
+        blocks, a, bnd = ti.markov_precond_blocks(w.extra["Q"], shift_frac=frac)
+        P = g.Precond.for_interval(a, bnd, 1e-2, [torch.as_tensor(B, device="cuda") for B in blocks])
+        kw = dict(maxit=p["maxit"], tol=p["tol"], rmax=80, mode=mval, s=p["s"], eta=p["eta"],
+                  r_sol=80, oversample=p["oversample"], seed=0, max_restarts=10)
+        g.tt_spgmres_solve(op, P, b, **kw)  # warm
+        ts = []
+        for _ in range(2):
+            flush.fill_(1)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            x, inf = g.tt_spgmres_solve(op, P, b, **kw)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1) * 1e-3)
+        mk[mname] = {"seconds": statistics.median(ts), "iters": inf["iters"],
+                     "cycles": inf["cycles"], "true_res": inf["true_res"],
+                     "max_rank": inf["max_rank"], "precond_terms": len(P.alpha),
+                     "shift_of_gap": frac}
+    out["markov_d5_n128_preconditioned_rank80"] = mk
     # differentiable workload: forward solve + adjoint solve + backward contractions
     w = ti.workload("differentiable")
     p = w.params

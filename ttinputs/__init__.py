@@ -33,6 +33,9 @@ __all__ = [
     "khatri_rao_factors",
     "gaussian_drm",
     "uneven_ranks",
+    "birth_death_generator",
+    "markov_operator",
+    "markov_precond_blocks",
     "Workload",
     "workload",
 ]
@@ -181,6 +184,101 @@ def uneven_ranks(d: int, lo: int, hi: int, seed: int) -> list:
     return [1] + [int(r) for r in inner] + [1]
 
 
+def birth_death_generator(n: int, rng) -> np.ndarray:
+    """Generator (row convention, rows sum to zero) of a random walk on states
+    0..n-1: rate eta_k from k to k+1 and mu_k from k to k-1, each drawn
+    i.i.d. uniformly from [1, 2] (Section 5.1.2)."""
+    eta = rng.uniform(1.0, 2.0, size=n - 1)
+    mu = rng.uniform(1.0, 2.0, size=n - 1)
+    Q = np.zeros((n, n))
+    for k in range(n - 1):
+        Q[k, k + 1] = eta[k]
+        Q[k + 1, k] = mu[k]
+    Q[np.arange(n), np.arange(n)] = -Q.sum(axis=1)
+    return Q
+
+
+def markov_operator(d: int, n: int, seed: int, sync_rate: float = 0.1):
+    """TT operator of the steady-state system of d coupled random walks
+    (Section 5.1.2), in the rank-one-normalised form
+    ``A = -G_c + 1 1^T / n^d`` with ``G_c = (Q + W - D)^T`` the generator in
+    column convention (``G_c pi = 0`` at steady state):
+
+    * ``Q = sum_k I x .. x Q_k x .. x I`` with Q_k from
+      :func:`birth_death_generator` (drawn in mode order from ``seed``);
+    * for every pair of neighbouring systems (k, k+1) the joint transition from
+      (n-2, n-2) to (n-1, n-1) at rate ``sync_rate`` (W) and its diagonal
+      outflow (D), i.e. ``sync_rate (M x M - E x E)`` in column convention with
+      ``M = e_{n-1} e_{n-2}^T`` and ``E = e_{n-2} e_{n-2}^T``;
+    * the rank-one term ``1 1^T / n^d = (J/n) x .. x (J/n)``, J all ones.
+
+    ``A rho = 1`` has the solution ``rho = n^d pi`` with pi the steady-state
+    distribution.  Cores ``[R_{k-1}, n, n, R_k]`` with ranks 5 (channels: 0
+    all terms closed, 1 none opened, 2 and 3 a synchronisation's W and D parts
+    opened at the previous mode, 4 the rank-one term).  Returns the cores and
+    the d matrices Q_k (row convention)."""
+    rng = np.random.default_rng(seed)
+    Qs = [birth_death_generator(n, rng) for _ in range(d)]
+    eye = np.eye(n)
+    M = np.zeros((n, n))
+    M[n - 1, n - 2] = 1.0
+    E = np.zeros((n, n))
+    E[n - 2, n - 2] = 1.0
+    J = np.ones((n, n)) / n
+    cores = []
+    for k in range(d):
+        Rl = 1 if k == 0 else 5
+        Rr = 1 if k == d - 1 else 5
+        c = np.zeros((Rl, n, n, Rr))
+        # left index: 0 closed, 1 none opened, 2 W open, 3 D open, 4 rank-one
+        # (the first core's single row acts as both "none opened" and the
+        # start of the rank-one channel)
+        left = {0: 0, 1: 1, 2: 2, 3: 3, 4: 4} if k > 0 else {1: 0, 4: 0}
+        last = k == d - 1
+        def put(a, b, mat):
+            if a in left:
+                c[left[a], :, :, 0 if last else b] += mat
+        single = -Qs[k].T
+        put(0, 0, eye)
+        put(1, 0, single)
+        if not last:
+            put(1, 1, eye)
+            put(1, 2, -sync_rate * M)
+            put(1, 3, sync_rate * E)
+        put(2, 0, M)
+        put(3, 0, E)
+        put(4, 4, J)
+        if last:
+            # the channels that are still open close here
+            pass
+        cores.append(c)
+    return cores, Qs
+
+
+def markov_precond_blocks(Qs, shift_frac: float = 1.0):
+    """Input data of the exponential-sum preconditioner of the Markov system:
+    the blocks ``A_k = -Q_k^T + (sigma / d) I`` of the shifted independent part
+    ``-Q^T + sigma I`` (the Kronecker sum of the systems' generators ignoring
+    the synchronisations, shifted off its zero eigenvalue), with sigma a
+    fraction of the smallest spectral gap among the systems, and the
+    interval ``[sigma, sigma + sum_k lambda_max(-Q_k)]`` that holds the
+    Kronecker sum's spectrum (the walks are reversible, so each -Q_k has real
+    eigenvalues).  The default shift is the whole gap: a smaller one lowers
+    the FP64 iteration count a little (6 against 9 at d = 5, n = 32) but
+    amplifies the near-null direction by 1/sigma, which the float modes'
+    products cannot resolve (TF32 stalled near 5e-6 at a third of the gap).
+    Returns ``(blocks, a, b)``."""
+    d = len(Qs)
+    gaps, tops = [], []
+    for Q in Qs:
+        ev = np.sort(np.linalg.eigvals(-Q.T).real)
+        gaps.append(ev[1])
+        tops.append(ev[-1])
+    sigma = shift_frac * min(gaps)
+    blocks = [-Q.T + (sigma / d) * np.eye(Q.shape[0]) for Q in Qs]
+    return blocks, sigma, sigma + sum(tops)
+
+
 class Workload:
     """One synthetic linear system ``A x = b`` in TT format plus the solver
     parameters it is quoted with."""
@@ -215,6 +313,11 @@ def workload(name: str, **over) -> Workload:
       m<=100, s=200, rank cap 150 (basis and solution): the solutions of these
       rough right-hand sides need it for a 1e-6 residual (caps 40, 64, 100 left
       most of them above 1e-6, and 128 some of those with ranks near 12).
+    * ``markov``  d=5, n=32 coupled random walks (Section 5.1.2), the
+      rank-one-normalised steady-state system ``(-G_c + 1 1^T / n^d) rho = 1``
+      (see :func:`markov_operator`), b = all ones (rank 1), rmax 64, m<=100;
+      solved with the exponential-sum preconditioner of
+      :func:`markov_precond_blocks`.
     * ``differentiable``  d=12, n=64, ``A(theta) = sum_k theta_k L_k`` with
       ``theta_k ~ U[0.5, 2]``, b and x_target random TT rank 4, rmax 64.
       x_target is scaled by ``1 / lambda_min(A(theta))`` (the largest gain of
@@ -257,6 +360,14 @@ def workload(name: str, **over) -> Workload:
         params = dict(maxit=maxit, s=2 * maxit, tol=1e-6, round_tol=1e-8, rmax=150, oversample=10,
                       mode="mixed", r_sol=150)
         return Workload(name, op, bs, {**params, **over.get("params", {})})
+    if name == "markov":
+        d, n = over.get("d", 5), over.get("n", 32)
+        op, Qs = markov_operator(d, n, seed=over.get("seed", 5))
+        b = rank_one_tt([np.ones(n)] * d)
+        maxit = over.get("maxit", 100)
+        params = dict(maxit=maxit, s=2 * maxit, tol=1e-6, rmax=64, oversample=10, mode="mixed",
+                      eta=0.1, r_sol=64)
+        return Workload(name, op, b, {**params, **over.get("params", {})}, extra=dict(Q=Qs))
     if name == "differentiable":
         d, n = over.get("d", 12), over.get("n", 64)
         rng = np.random.default_rng(over.get("theta_seed", 4))
