@@ -476,9 +476,8 @@ size_t tt_spgmres_solve_workspace(const tt_op* A, const tt_precond* P, const tt_
  * Measurement support (no counterpart in the method): tt_profile(mask) clears
  * the launch records and, for every class bit set in mask (1 CUDA-core GEMM,
  * 2 FP64 Householder QR, 4 Jacobi SVD, 8 least squares, 16 copies / generators,
- * 32 FP64 Gram, 64 FP64 Cholesky, 128 tensor-core), brackets each later launch
- * of that class with CUDA
- * events on its stream; 128 selects the tcgen05 tensor-core contractions.
+ * 32 FP64 Gram, 64 FP64 Cholesky, 128 tensor-core matvec), brackets each later
+ * launch of that class with CUDA events on its stream.
  * tt_profile_read synchronises those events and returns, for one class index
  * (0..7), the summed
  * event time in milliseconds, the number of launches and their algorithmic

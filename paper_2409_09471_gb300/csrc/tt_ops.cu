@@ -41,6 +41,7 @@ void check_device_flags(const Ctx& c) {
   if (g_dry_run) return;
   const int h = read_int(c, c.err);
   if (h & 1) throw Error(TT_ERR_TIMEOUT, "a grid barrier of the FP64 QR timed out");
+  if (h & 4) throw Error(TT_ERR_TIMEOUT, "an mbarrier wait of a tensor-core kernel timed out");
 }
 
 // ------------------------------------------------------------------ matvec

@@ -110,7 +110,7 @@ def test_matvec_full_size_eigenvector(g, mode):
         assert abs(ott.entry(yc, idx) - mu * ott.entry(q, idx)) <= 50 * tol_of(g, mode) * scale
 
 
-@pytest.mark.parametrize("mode", [0, 1])
+@pytest.mark.parametrize("mode", [0, 1, 2])
 @pytest.mark.parametrize("s,ns,ranks", [(100, [16] * 4, [1, 4, 7, 3, 1]),
                                         (67, [70, 3, 65], [1, 65, 2, 1]),
                                         (1, [5, 5], [1, 2, 1])])
@@ -134,7 +134,7 @@ def test_sketch_full_size_rank_one(g):
     assert rel_err(out.cpu().numpy(), expect) <= F64_TOL
 
 
-@pytest.mark.parametrize("mode", [0, 1])
+@pytest.mark.parametrize("mode", [0, 1, 2])
 def test_dot_parity(g, mode):
     ns = [13, 64, 7, 30]
     x = ti.random_tt(ns, [1, 5, 70, 3, 1], seed=6)
@@ -177,7 +177,7 @@ def test_lstsq_parity(g, s, k):
     assert rel_err(W @ y.cpu().numpy(), W @ y_ref) <= 1e-9
 
 
-@pytest.mark.parametrize("mode", [0, 1])
+@pytest.mark.parametrize("mode", [0, 1, 2])
 def test_round_rand_identity_tol0(g, mode):
     ns = [6, 9, 5, 7]
     x = ti.random_tt(ns, [1, 3, 7, 4, 1], seed=8)
@@ -189,7 +189,7 @@ def test_round_rand_identity_tol0(g, mode):
     assert tt_rel_diff(y.numpy(), x) <= 10 * tol_of(g, mode)
 
 
-@pytest.mark.parametrize("mode", [0, 1])
+@pytest.mark.parametrize("mode", [0, 1, 2])
 @pytest.mark.parametrize("eps,rmax,p", [(1e-6, 30, 10), (1e-2, 30, 5), (0.0, 4, 3), (1e-8, 2, 0)])
 def test_round_rand_parity_same_drm(g, mode, eps, rmax, p):
     ns = [8, 70, 5, 9]
@@ -320,3 +320,30 @@ def test_round_rand_float_truncation_vs_sequential_tt_svd(g, mode, seed):
     T = ott.add(terms)
     assert tt_rel_diff(y.numpy(), T) <= eps + 1e-5
     assert tt_rel_diff(y.numpy(), ref) <= 2 * eps + 1e-5
+
+
+def test_tf32_contractions_ragged_ranks(g):
+    # TF32 mode runs the sketch steps, Gram sweeps and the rounding's
+    # contractions on the tcgen05 grouped GEMM (split TF32, FP32 accumulation)
+    # once a problem is large enough: ragged bond ranks 1, 9, 65, 74, 130 give
+    # partial tiles in every dimension, transposed problems and split-K
+    ns = [16, 32, 8, 64, 12]
+    ranks = [1, 9, 65, 74, 130, 1]
+    x = ti.random_tt(ns, ranks, seed=90)
+    y = ti.random_tt(ns, [1, 12, 70, 66, 9, 1], seed=91)
+    X, Y = dev_tt(g, x, 2), dev_tt(g, y, 2)
+    S = ti.khatri_rao_factors(ns, 160, seed=92)
+    out = g.tt_sketch(X, [torch.as_tensor(f, dtype=torch.float32, device="cuda") for f in S],
+                      mode=2)
+    assert rel_err(out.cpu().numpy(), ott.sketch_kr_fast(x, S)) <= 10 * TF32_TOL
+    dv = g.tt_dot(X, Y, mode=2).item()
+    assert abs(dv - ott.dot(x, y)) <= 10 * TF32_TOL * ott.norm(x) * ott.norm(y)
+    drm = ti.gaussian_drm(ns, [1, 80, 80, 80, 80, 1], seed=93)
+    terms = [(1.0, x), (-0.5, y)]
+    ref = ornd.rto_round(terms, drm, eps=1e-6, rmax=70, oversample=10,
+                         truncation="simultaneous")
+    r = g.tt_round_rand([X, Y], [1.0, -0.5], 1e-6, 70, 10,
+                        drm=[torch.as_tensor(c, dtype=torch.float32, device="cuda") for c in drm],
+                        mode=2)
+    assert r.ranks == ott.ranks(ref)
+    assert tt_rel_diff(r.numpy(), ref) <= 1e-4
