@@ -148,8 +148,15 @@ SolveResult sgmres_solve(const Ctx& c0, const TTop<double>& A64in, const TTv<dou
     wcap[k] = A64.R[k] * std::max(vcap[k], xcap[k]);
     bcap[k] = b.r[k];
   }
+  // Krylov basis.  With the STTA correction (final_stta) a basis vector is
+  // sketched when it is formed and afterwards read only by the Gram-Schmidt
+  // window of the next ell steps, so ell + 1 slots used as a ring hold all
+  // that is live; the rounding form keeps the whole basis for Round(sum y_i v_i).
+  const int ell = std::max(1, std::min(p.ell, p.maxit));
+  const int nslots = p.final_stta ? ell + 1 : p.maxit + 1;
   std::vector<TTv<T>> V;
-  for (int i = 0; i <= p.maxit; ++i) V.push_back(alloc_tt<T>(ar, d, n, vcap.data()));
+  for (int i = 0; i < nslots; ++i) V.push_back(alloc_tt<T>(ar, d, n, vcap.data()));
+  auto VS = [&](int i) -> TTv<T>& { return V[i % nslots]; };
   TTv<T> w = alloc_tt<T>(ar, d, n, wcap.data());
   TTv<T> bT = f64 ? TTv<T>() : alloc_tt<T>(ar, d, n, bcap.data());
   TTv<T> rhs = alloc_tt<T>(ar, d, n, vcap.data());
@@ -171,7 +178,6 @@ SolveResult sgmres_solve(const Ctx& c0, const TTop<double>& A64in, const TTv<dou
   double* Wm = ar.take<double>(s * p.maxit);
   double* Sr0 = ar.take<double>(s);
   double* ydev = ar.take<double>(p.maxit);
-  const int ell = std::max(1, std::min(p.ell, p.maxit));
   double* hcoef = ar.take<double>(p.maxit);  // h_{i,k} of the older vectors (ell > 1)
   double* scal = ar.take<double>(16);  // 0 beta, 1 h, 2 ||v~||^2, 3 ||v~||, 4 res, 5 ||Sr0||^2, 6 ||Sr0||
   double* lsws = (double*)ar.take<char>((int64_t)lstsq_workspace(s, p.maxit));
@@ -257,9 +263,9 @@ SolveResult sgmres_solve(const Ctx& c0, const TTop<double>& A64in, const TTv<dou
     for (int k = 0; k < d; ++k) ps[k] = skb + (int64_t)i * ssz + psi_off[k];
     for (int k = 0; k + 1 < d; ++k) os[k] = skb + (int64_t)i * ssz + om_off[k];
     if constexpr (std::is_same<T, double>::value) {
-      tt_stta_sketch_dev<double>(c64, V[i], 1.0, 0, Xv, Yv, ps.data(), os.data());
+      tt_stta_sketch_dev<double>(c64, VS(i), 1.0, 0, Xv, Yv, ps.data(), os.data());
     } else {
-      copy_tt(V[i], vs64, nullptr, 0);
+      copy_tt(VS(i), vs64, nullptr, 0);
       tt_stta_sketch_dev<double>(c64, vs64, 1.0, 0, Xv, Yv, ps.data(), os.data());
     }
   };
@@ -307,9 +313,11 @@ SolveResult sgmres_solve(const Ctx& c0, const TTop<double>& A64in, const TTv<dou
     t2[0].X = w;
     for (int i = 0; i < ell; ++i) t2[1 + i].X = V[i];
     tt_round_rand_dev<T>(c, t2, 0.1, p.rmax, p.oversample, drm, V[ell]);
-    std::vector<Term<T>> tk(p.maxit);
-    for (int i = 0; i < p.maxit; ++i) tk[i].X = V[i];
-    tt_round_rand_dev<T>(c, tk, 0.1, r_sol, p.oversample, drm, e);
+    if (!use_stta) {
+      std::vector<Term<T>> tk(p.maxit);
+      for (int i = 0; i < p.maxit; ++i) tk[i].X = V[i];
+      tt_round_rand_dev<T>(c, tk, 0.1, r_sol, p.oversample, drm, e);
+    }
     for (int q = 0; q <= d; ++q) { e64.r[q] = xcap[q]; w64.r[q] = wcap[q]; }
     std::vector<Term<double>> u2(2);
     u2[0].X = x; u2[1].X = e64;
@@ -355,9 +363,9 @@ SolveResult sgmres_solve(const Ctx& c0, const TTop<double>& A64in, const TTv<dou
     for (int k = 0; k < p.maxit; ++k) {
       if (use_stta) stta_sketch_basis(k);
       // w = A v_k, or A P^{-1} v_k with P^{-1} v_k rounded to rmax
-      const TTv<T>* av = &V[k];
+      const TTv<T>* av = &VS(k);
       if (use_pre) {
-        precond_apply_dev<T>(c, pd, V[k], round_tol, p.rmax, p.oversample, drm, pbufs, z);
+        precond_apply_dev<T>(c, pd, VS(k), round_tol, p.rmax, p.oversample, drm, pbufs, z);
         av = &z;
       }
       for (int q = 0; q <= d; ++q) w.r[q] = A64.R[q] * av->r[q];
@@ -371,21 +379,21 @@ SolveResult sgmres_solve(const Ctx& c0, const TTop<double>& A64in, const TTv<dou
       terms[0].X = w;
       for (int i = first; i <= k; ++i) {
         double* hi = i == k ? scal + 1 : hcoef + i;
-        tt_dot_dev<T>(c, w, V[i], hi);
+        tt_dot_dev<T>(c, w, VS(i), hi);
         Term<T>& t = terms[1 + i - first];
-        t.X = V[i];
+        t.X = VS(i);
         t.coef = -1.0;
         t.coef_dev = hi;
       }
-      tt_round_rand_dev<T>(c, terms, round_tol, p.rmax, p.oversample, drm, V[k + 1]);
+      tt_round_rand_dev<T>(c, terms, round_tol, p.rmax, p.oversample, drm, VS(k + 1));
       // h_{k+1,k} = ||v~||: the norm of core 1 when cores 2..d are
       // right-orthogonal (FP64 mode), otherwise the Gram sweep
-      if (f64) sumsq(V[k + 1].core[0], f64, V[k + 1].core_elems(0), scal + 2, c.scratch + 16, c.st);
-      else tt_dot_dev<T>(c, V[k + 1], V[k + 1], scal + 2);
+      if (f64) sumsq(VS(k + 1).core[0], f64, VS(k + 1).core_elems(0), scal + 2, c.scratch + 16, c.st);
+      else tt_dot_dev<T>(c, VS(k + 1), VS(k + 1), scal + 2);
       sqrt_scalar(scal + 2, scal + 3, c.st);
       {
         CopySeg sg;
-        sg.src = V[k + 1].core[0]; sg.dst = V[k + 1].core[0]; sg.A = V[k + 1].core_elems(0);
+        sg.src = VS(k + 1).core[0]; sg.dst = VS(k + 1).core[0]; sg.A = VS(k + 1).core_elems(0);
         sg.sa = 1; sg.src_f64 = f64; sg.dst_f64 = f64; sg.scale_dev = scal + 3; sg.scale_dev_inv = 1;
         copy3d({sg}, c.st);
       }
@@ -399,8 +407,8 @@ SolveResult sgmres_solve(const Ctx& c0, const TTop<double>& A64in, const TTv<dou
       const double hv[2] = {hs4[2], hs4[3]};
       sres = betaS > 0 ? hv[1] / betaS : 0.0;
       res.res_hist.push_back(sres);
-      res.rank_hist.push_back(V[k + 1].max_rank());
-      res.max_rank = std::max(res.max_rank, V[k + 1].max_rank());
+      res.rank_hist.push_back(VS(k + 1).max_rank());
+      res.max_rank = std::max(res.max_rank, VS(k + 1).max_rank());
       kdone = k + 1;
       ++res.iters;
       // h_{k+1,k} = 0 to working precision: ||v~|| at the rounding level of
