@@ -59,7 +59,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--mode", choices=["tf32", "fp32", "fp64"], default=None)
+    ap.add_argument("--mode", choices=["tf32", "bf16", "fp32", "fp64"], default=None)
     ap.add_argument("--no-fp64-leg", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true",
                     help="skip the host oracle solve of the GPU arm")
@@ -306,7 +306,8 @@ def timed_solves(torch, g, op, b, kw, ws, steps, flush, stream):
 
 def extra_configs(torch, g, flush, stream, modes):
     """The other configurations' solves (not part of the headline): the FP64
-    Laplacian (d = 4, n = 16), the large-rank Laplacian (d = 20, n = 128, rank
+    Laplacian (d = 4, n = 16), the headline system in split-BF16 mode, the
+    large-rank Laplacian (d = 20, n = 128, rank
     cap 128) in the mixed mode and in FP64, the preconditioned Markov-chain
     system (d = 5, n = 128) in FP64 and FP32, and one forward + adjoint
     solve of the differentiable workload (d = 12, n = 64)."""
@@ -331,6 +332,8 @@ def extra_configs(torch, g, flush, stream, modes):
                 "true_res": inf["true_res"], "max_rank": inf["max_rank"], "runs": reps}
 
     out["laplace_fp64_d4_n16"] = {"fp64": solve_cfg("laplace_fp64", g.MODE_FP64, 3)}
+    # the headline workload with the split-BF16 tensor-core matvec
+    out["convdiff_d10_n64_bf16"] = {"bf16": solve_cfg("convdiff", g.MODE_BF16, 3)}
     lr = {}
     for mname in modes:
         lr[mname] = solve_cfg("large_rank", {"tf32": g.MODE_TF32, "fp32": g.MODE_FP32,
@@ -428,7 +431,8 @@ def run_ours(args):
         cpu = oracle_full_solve(w, p)
 
     mode_name = args.mode or os.environ.get("TTSG_MODE", "tf32")
-    mode = {"tf32": g.MODE_TF32, "fp32": g.MODE_FP32, "fp64": g.MODE_FP64}[mode_name]
+    mode = {"tf32": g.MODE_TF32, "fp32": g.MODE_FP32, "fp64": g.MODE_FP64,
+            "bf16": g.MODE_BF16}[mode_name]
     op = g.op_to_device(w.op)
     b = g.TT.from_numpy(w.b)
     kw = dict(maxit=p["maxit"], tol=p["tol"], rmax=p["rmax"], s=p["s"], eta=p["eta"],
@@ -559,7 +563,8 @@ def run_ours(args):
     line = {"metric": METRIC, "value": value, "unit": "s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None,
-            "dtype": {"tf32": "tf32+f64", "fp32": "f32+f64", "fp64": "f64"}[mode_name],
+            "dtype": {"tf32": "tf32+f64", "bf16": "bf16+f64", "fp32": "f32+f64",
+                      "fp64": "f64"}[mode_name],
             "data": "synthetic",
             "config": {"workload": WORKLOAD, "mode": mode_name, "parallelism": "replicas",
                        "l2": "flushed (512 MiB write) before every step"},

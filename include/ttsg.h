@@ -28,6 +28,11 @@
  *                 accumulation, about 2^-20 relative error per product);
  *                 the other contractions as in TT_MODE_FP32; QR, least
  *                 squares and residual checks in FP64.
+ *   TT_MODE_BF16  as TT_MODE_TF32 with the matvec's tensor-core products in
+ *                 split BF16 (each FP32 operand as bf16 hi + bf16 lo, three
+ *                 kind::f16 products, FP32 accumulation, about 2^-17 relative
+ *                 per product; plain BF16, 2^-9, could not contract the
+ *                 refinement of these operators).
  * Streams.  ``stream`` is a cudaStream_t (NULL = default stream).  Calls that
  *   return host values or data-dependent ranks synchronise that stream.
  * Workspace.  Entry points that need scratch take ``ws`` (device) and
@@ -69,6 +74,7 @@ extern "C" {
 #define TT_MODE_FP64 0
 #define TT_MODE_FP32 1
 #define TT_MODE_TF32 2
+#define TT_MODE_BF16 3
 
 #define TT_MAX_D 64
 

@@ -25,10 +25,11 @@ import numpy as np
 import torch
 
 from ._abi import (lib, TTVec, TTVecOut, TTOp, TTPrecond, SolverParams, SolverInfo, MODE_FP64,
-                   MODE_FP32, MODE_TF32, TTError, check, LIB_PATH)
+                   MODE_FP32, MODE_TF32, MODE_BF16, TTError, check, LIB_PATH)
 
 __all__ = ["TT", "tt_matvec", "tt_sketch", "tt_sketch_factors", "tt_dot", "tt_round_rand", "tt_gaussian", "tt_qr_f64",
-           "tt_lstsq_f64", "tt_sgmres_solve", "MODE_FP64", "MODE_FP32", "MODE_TF32", "TTError",
+           "tt_lstsq_f64", "tt_sgmres_solve", "MODE_FP64", "MODE_FP32", "MODE_TF32", "MODE_BF16",
+           "TTError",
            "LIB_PATH", "mode_dtype", "op_to_device", "tt_dot_grad", "tt_local_dots",
            "tt_kron_sum_op", "tt_op_transpose", "solve_loss", "tt_qr_f64_batched",
            "tt_sgmres_solve_batched", "tt_stta_sketch", "tt_stta_recover", "Precond",

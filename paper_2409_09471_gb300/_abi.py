@@ -8,7 +8,7 @@ import os
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libttsg.so")
 
-MODE_FP64, MODE_FP32, MODE_TF32 = 0, 1, 2
+MODE_FP64, MODE_FP32, MODE_TF32, MODE_BF16 = 0, 1, 2, 3
 STATUS = {0: "TT_OK", 1: "TT_ERR_ARG", 2: "TT_ERR_WORKSPACE", 3: "TT_ERR_CUDA",
           4: "TT_ERR_TIMEOUT", 5: "TT_ERR_NOT_CONVERGED", 6: "TT_ERR_UNSUPPORTED",
           7: "TT_ERR_BREAKDOWN"}

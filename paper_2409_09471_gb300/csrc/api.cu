@@ -36,7 +36,8 @@ int guarded(F&& f) {
 }
 
 int check_mode(int mode) {
-  if (mode != TT_MODE_FP64 && mode != TT_MODE_FP32 && mode != TT_MODE_TF32)
+  if (mode != TT_MODE_FP64 && mode != TT_MODE_FP32 && mode != TT_MODE_TF32 &&
+      mode != TT_MODE_BF16)
     throw Error(TT_ERR_ARG, "unknown mode " + std::to_string(mode));
   return mode;
 }

@@ -141,7 +141,9 @@ struct TcCoreArgs {
   float* G;         // output core
   int64_t n, R0, R1, r0, r1;
 };
-void matvec_tc_cores(const std::vector<TcCoreArgs>& cores, int* err, cudaStream_t st);
+// bf16: the split-BF16 kernel (TT_MODE_BF16) instead of split TF32.
+void matvec_tc_cores(const std::vector<TcCoreArgs>& cores, int* err, cudaStream_t st,
+                     bool bf16 = false);
 // Device scratch for split-K partial sums (set per API call; null disables split-K).
 void set_gemm_scratch(void* ws, size_t bytes);
 constexpr size_t GEMM_SCRATCH_BYTES = size_t(48) << 20;

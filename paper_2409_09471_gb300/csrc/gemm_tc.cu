@@ -1,5 +1,6 @@
-// Tensor-core contractions for TT_MODE_TF32: the TT matvec core contraction
-// (Section 2.2, matvec formula) on tcgen05 in TF32 with FP32 accumulation.
+// Tensor-core contractions for TT_MODE_TF32 and TT_MODE_BF16: the TT matvec
+// core contraction (Section 2.2, matvec formula) on tcgen05 in split TF32 or
+// split BF16 with FP32 accumulation.
 //
 // Per core k the contraction is a batch over (a, l) of GEMMs
 //   G[(a,l)][(i,a')][l'] = sum_j Dp[a][(i,a')][j] * Ct[l][l'][j],
@@ -28,6 +29,7 @@
 #include "prof.cuh"
 #include <cuda.h>
 #include <cudaTypedefs.h>
+#include <cuda_bf16.h>
 
 namespace ttsg {
 
@@ -280,6 +282,194 @@ matvec_tc_kernel(const __grid_constant__ TcBatch b) {
   }
 }
 
+// Instruction descriptor for kind::f16 with BF16 operands: D F32, A and B
+// BF16, both K-major.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+  return (1u << 4)             // D format F32
+         | (1u << 7)           // A format BF16
+         | (1u << 10)          // B format BF16
+         | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+// Split BF16 form of the same contraction (TT_MODE_BF16): every FP32 value x is
+// split into hi = bf16(x) and lo = bf16(x - hi) (round to nearest; 8 + 8
+// significant bits) and the MMAs accumulate hi*hi + hi*lo + lo*hi in FP32.  The
+// dropped lo*lo term and the rounding of lo are about 2^-17 relative per
+// product.  A 64-wide K chunk arrives as two 32-float TMA boxes per operand
+// (the tensor maps of the TF32 kernel); the split writes the bf16 tiles in the
+// 128-byte-swizzled K-major layout of 16-bit operands (64 values per 128-byte
+// row: element (r, k) at r * 64 + ((k / 8) ^ (r % 8)) * 8 + k % 8), and each
+// MMA (kind::f16, M = 128, N = 64) takes 16 of the chunk's K values.
+constexpr int BK16 = 64;
+__global__ void __launch_bounds__(TC_THREADS, 1)
+matvec_bf16_kernel(const __grid_constant__ TcBatch b) {
+  if ((int)blockIdx.z >= b.count) return;
+  const TcCore& p = b.c[blockIdx.z];
+  const CUtensorMap& mapA = p.mA;
+  const CUtensorMap& mapB = p.mB;
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* base = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  // FP32 boxes [A k0 | A k0+32 | B k0 | B k0+32], then bf16 [A hi | A lo | B hi | B lo]
+  float* fA = (float*)base;                          // 2 x [TM][TK]
+  float* fB = fA + 2 * TM * TK;                      // 2 x [TN][TK]
+  uint16_t* hA = (uint16_t*)(fB + 2 * TN * TK);      // [TM][64]
+  uint16_t* lA = hA + TM * BK16;
+  uint16_t* hB = lA + TM * BK16;                     // [TN][64]
+  uint16_t* lB = hB + TN * BK16;
+  __shared__ __align__(8) uint64_t bar_full, bar_mma;
+  __shared__ uint32_t tmem_base;
+  __shared__ int fail;
+
+  const int tiles_m = (p.M + TM - 1) / TM, tiles_n = (p.N + TN - 1) / TN;
+  const int tm = blockIdx.x % tiles_m, tn = blockIdx.x / tiles_m;
+  if (tn >= tiles_n || (int)blockIdx.y >= p.R0 * p.r0) return;
+  const int a = blockIdx.y / p.r0, l = blockIdx.y % p.r0;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(&tmem_base)),
+                 "r"(TN));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (threadIdx.x == 0) {
+    fail = 0;
+    mbar_init(&bar_full, 1);
+    mbar_init(&bar_mma, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_base;
+
+  // one operand tile: rows x 64 FP32 values (two swizzled boxes) -> bf16 hi/lo;
+  // each thread converts 4 consecutive K values (one 16-byte chunk of a box)
+  auto split_tile = [&](const float* f, uint16_t* hi, uint16_t* lo, int rows) {
+    for (int e = threadIdx.x; e < rows * (BK16 / 4); e += TC_THREADS) {
+      const int r = e >> 4, kq = e & 15;            // 16 chunks of 4 per row
+      const int bx = kq >> 3, c32 = kq & 7;
+      const float4 v = *reinterpret_cast<const float4*>(f + bx * rows * TK + r * TK +
+                                                         ((c32 ^ (r & 7)) << 2));
+      const float xs[4] = {v.x, v.y, v.z, v.w};
+      uint16_t hs[4], ls[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const __nv_bfloat16 h = __float2bfloat16_rn(xs[q]);
+        const __nv_bfloat16 lo16 = __float2bfloat16_rn(xs[q] - __bfloat162float(h));
+        hs[q] = __bfloat16_as_ushort(h);
+        ls[q] = __bfloat16_as_ushort(lo16);
+      }
+      const int k = kq * 4;
+      const int o = r * BK16 + ((((k >> 3) ^ (r & 7))) << 3) + (k & 7);
+      *reinterpret_cast<uint2*>(hi + o) = make_uint2(hs[0] | ((uint32_t)hs[1] << 16),
+                                                     hs[2] | ((uint32_t)hs[3] << 16));
+      *reinterpret_cast<uint2*>(lo + o) = make_uint2(ls[0] | ((uint32_t)ls[1] << 16),
+                                                     ls[2] | ((uint32_t)ls[3] << 16));
+    }
+  };
+
+  const int ktiles = (p.K + BK16 - 1) / BK16;
+  const int rowA = a * p.M + tm * TM;
+  const int rowB = l * p.N + tn * TN;
+  uint32_t phase = 0;
+  int stage = 0;
+  for (int kt = 0; kt < ktiles; ++kt) {
+    if (threadIdx.x == 0) {
+      mbar_expect_tx(&bar_full, 2 * (TM + TN) * TK * 4);
+      tma_load_2d(fA, &mapA, &bar_full, kt * BK16, rowA);
+      tma_load_2d(fA + TM * TK, &mapA, &bar_full, kt * BK16 + TK, rowA);
+      tma_load_2d(fB, &mapB, &bar_full, kt * BK16, rowB);
+      tma_load_2d(fB + TN * TK, &mapB, &bar_full, kt * BK16 + TK, rowB);
+    }
+    stage = 1;
+    const bool landed = mbar_wait(&bar_full, phase);
+    if (__syncthreads_or(!landed)) break;
+    split_tile(fA, hA, lA, TM);
+    split_tile(fB, hB, lB, TN);
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t idesc = idesc_bf16(TM, TN);
+      const uint64_t dA[2] = {smem_desc_sw128(smem_u32(hA)), smem_desc_sw128(smem_u32(lA))};
+      const uint64_t dB[2] = {smem_desc_sw128(smem_u32(hB)), smem_desc_sw128(smem_u32(lB))};
+#pragma unroll
+      for (int kk = 0; kk < BK16 / 16; ++kk) {
+        // advance 16 BF16 values (32 bytes) along K inside the swizzle row
+        const uint64_t off = (uint64_t)((kk * 32) >> 4);
+#pragma unroll
+        for (int t = 0; t < 3; ++t) {
+          // t = 0: hi*hi, 1: lo*hi, 2: hi*lo
+          const uint64_t da = dA[t == 1 ? 1 : 0] + off;
+          const uint64_t db = dB[t == 2 ? 1 : 0] + off;
+          const uint32_t acc = (kt > 0 || kk > 0 || t > 0) ? 1u : 0u;
+          asm volatile(
+              "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
+              " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+              "l"(da), "l"(db), "r"(idesc), "r"(acc)
+              : "memory");
+        }
+      }
+      asm volatile(
+          "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+              smem_u32(&bar_mma))
+          : "memory");
+    }
+    stage = 2;
+    const bool done = mbar_wait(&bar_mma, phase);
+    if (__syncthreads_or(!done)) break;
+    stage = 0;
+    phase ^= 1u;
+  }
+  if (stage != 0 && threadIdx.x == 0) {
+    fail = 1;
+    atomicOr(b.err, 4);
+    mbar_wait(&bar_full, phase);
+    if (stage == 2) mbar_wait(&bar_mma, phase);
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+
+  float* St = (float*)base;
+  constexpr int LDS = TN + 1;
+  static_assert(TM * LDS * 4 <= 2 * (TM + TN) * TK * 4, "staging tile exceeds the FP32 boxes");
+  if (!fail) {
+    const int row = warp * 32 + lane;
+#pragma unroll
+    for (int c0 = 0; c0 < TN; c0 += 16) {
+      uint32_t r[16];
+      const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x16.b32"
+          " {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+          : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+            "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+            "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+          : "r"(taddr));
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+      for (int q = 0; q < 16; ++q) St[row * LDS + c0 + q] = __uint_as_float(r[q]);
+    }
+  }
+  __syncthreads();
+  if (!fail) {
+    const int64_t gbase = (int64_t)(a * p.r0 + l) * p.M * p.N;
+    for (int e = threadIdx.x; e < TM * TN; e += TC_THREADS) {
+      const int rr = e / TN, cc = e % TN;
+      const int m = tm * TM + rr, n = tn * TN + cc;
+      if (m < p.M && n < p.N) p.G[gbase + (int64_t)m * p.N + n] = St[rr * LDS + cc];
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TN));
+  }
+}
+
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
   if (!fn) {
@@ -321,12 +511,16 @@ bool matvec_tc_supported(int64_t n, int64_t r1) {
 // All tensor-core cores of one matvec: core k gives G_k (R0 r0 x n x R1 r1)
 // from Dp_k ([R0][n R1][n]) and Ct_k ([r0][r1][n]); up to TC_MAXC cores per
 // launch.
-void matvec_tc_cores(const std::vector<TcCoreArgs>& cores, int* err, cudaStream_t st) {
+void matvec_tc_cores(const std::vector<TcCoreArgs>& cores, int* err, cudaStream_t st, bool bf16) {
   if (g_dry_run || cores.empty()) return;
   const size_t smem = (size_t)2 * (TM + TN) * TK * 4 + 1024;
-  static const bool attr = [smem] {
+  // split BF16: the FP32 boxes of a 64-wide chunk plus the bf16 hi/lo tiles
+  const size_t smem16 = (size_t)2 * (TM + TN) * TK * 4 + (size_t)2 * (TM + TN) * BK16 * 2 + 1024;
+  static const bool attr = [smem, smem16] {
     TT_CUDA(cudaFuncSetAttribute(matvec_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)smem));
+    TT_CUDA(cudaFuncSetAttribute(matvec_bf16_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem16));
     return true;
   }();
   (void)attr;
@@ -351,9 +545,15 @@ void matvec_tc_cores(const std::vector<TcCoreArgs>& cores, int* err, cudaStream_
     }
     if (max_batch > 65535) throw Error(TT_ERR_UNSUPPORTED, "matvec_tc: batch too large");
     const int tok = prof_begin(PROF_TC, st);
-    matvec_tc_kernel<<<dim3((unsigned)max_tiles, (unsigned)max_batch, (unsigned)bt.count),
-                       TC_THREADS, smem, st>>>(bt);
-    check_launch("matvec_tc_kernel");
+    if (bf16) {
+      matvec_bf16_kernel<<<dim3((unsigned)max_tiles, (unsigned)max_batch, (unsigned)bt.count),
+                           TC_THREADS, smem16, st>>>(bt);
+      check_launch("matvec_bf16_kernel");
+    } else {
+      matvec_tc_kernel<<<dim3((unsigned)max_tiles, (unsigned)max_batch, (unsigned)bt.count),
+                         TC_THREADS, smem, st>>>(bt);
+      check_launch("matvec_tc_kernel");
+    }
     // algorithmic flops and bytes (one product; the split adds two more on
     // the tensor pipe)
     prof_end(tok, st, flops, bytes);

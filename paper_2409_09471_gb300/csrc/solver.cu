@@ -33,11 +33,13 @@ double read_double(cudaStream_t st, const double* dev) {
 
 // Mode-dependent floor of the per-cycle sketched tolerance: the accuracy the
 // contractions of that precision can deliver before a restart is needed
-// (TF32 mode: split-TF32 products, about 2^-20 relative each).
+// (TF32 mode: split-TF32 products, about 2^-20 relative each; BF16 mode:
+// split-BF16 products, about 2^-17).
 double inner_floor(int mode) {
   switch (mode) {
     case TT_MODE_FP64: return 0.0;
     case TT_MODE_FP32: return 1e-7;
+    case TT_MODE_BF16: return 1e-5;
     default: return 1e-6;
   }
 }

@@ -50,7 +50,7 @@ void check_device_flags(const Ctx& c) {
 template <typename T>
 void tt_matvec_dev(const Ctx& c, const TTop<T>& A, const TTv<T>& x, const TTv<T>& y) {
   std::vector<GemmProblem> ps;
-  if (c.mode == TT_MODE_TF32 && sizeof(T) == 4) {
+  if ((c.mode == TT_MODE_TF32 || c.mode == TT_MODE_BF16) && sizeof(T) == 4) {
     // tensor cores: Ct_k[l][l'][j] = C_k[l][j][l'] for every core (one copy
     // launch), then one tcgen05 launch for all of them
     const size_t mk = c.ar->mark();
@@ -67,7 +67,7 @@ void tt_matvec_dev(const Ctx& c, const TTop<T>& A, const TTv<T>& x, const TTv<T>
       tc.push_back(TcCoreArgs{(const float*)A.core[k], Ct, (float*)y.core[k], n, R0, R1, r0, r1});
     }
     copy3d(segs, c.st);
-    matvec_tc_cores(tc, c.err, c.st);
+    matvec_tc_cores(tc, c.err, c.st, c.mode == TT_MODE_BF16);
     c.ar->release(mk);
     for (int k = 0; k < x.d; ++k) {
       if (matvec_tc_supported(x.n[k], x.r[k + 1])) continue;

@@ -19,6 +19,7 @@ pytestmark = pytest.mark.gpu
 F64_TOL = 1e-12
 F32_TOL = 2e-5
 TF32_TOL = 3e-5   # split TF32 (hi*hi + lo*hi + hi*lo) with FP32 accumulation
+BF16_TOL = 1e-4   # split BF16: bf16 hi + lo (8 + 8 significant bits), ~2^-17 per product
 
 
 @pytest.fixture(scope="module")
@@ -38,7 +39,7 @@ def rel_err(a, b):
 
 
 def tol_of(g, mode):
-    return {0: F64_TOL, 1: F32_TOL, 2: TF32_TOL}[mode]
+    return {0: F64_TOL, 1: F32_TOL, 2: TF32_TOL, 3: BF16_TOL}[mode]
 
 
 def tt_rel_diff(a_cores, b_cores):
@@ -74,9 +75,11 @@ def test_matvec_parity(g, mode, d, n, ranks):
         assert rel_err(a, b) <= tol_of(g, mode)
 
 
+@pytest.mark.parametrize("mode", [2, 3])
 @pytest.mark.parametrize("d,n,ranks", [(3, 64, [1, 64, 37, 1]), (3, 16, [1, 5, 100, 1]),
-                                       (4, 32, [1, 1, 3, 130, 1]), (2, 128, [1, 9, 1])])
-def test_matvec_parity_tensor_cores(g, d, n, ranks):
+                                       (4, 32, [1, 1, 3, 130, 1]), (2, 128, [1, 9, 1]),
+                                       (3, 12, [1, 7, 3, 1])])
+def test_matvec_parity_tensor_cores(g, mode, d, n, ranks):
     # n a multiple of 4 takes the tcgen05 path in TF32 mode (two N tiles when
     # the rank exceeds 64, two M tiles when n R > 128)
     M = ti.laplacian_1d(n) + 10 * ti.central_difference_1d(n)
@@ -84,13 +87,15 @@ def test_matvec_parity_tensor_cores(g, d, n, ranks):
     op[1] = np.random.default_rng(3).standard_normal(op[1].shape)
     x = ti.random_tt([n] * d, ranks, seed=4)
     ref = ott.matvec(op, x)
-    y = g.tt_matvec(g.op_to_device(op, torch.float32), dev_tt(g, x, 2), mode=2)
+    # mode 2 split TF32; mode 3 split BF16 (a 64-wide K chunk per step, so
+    # n = 12 and 16 are one partial chunk and 128 two full ones)
+    y = g.tt_matvec(g.op_to_device(op, torch.float32), dev_tt(g, x, mode), mode=mode)
     assert y.ranks == ott.ranks(ref)
     for a, b in zip(y.numpy(), ref):
-        assert rel_err(a, b) <= TF32_TOL
+        assert rel_err(a, b) <= tol_of(g, mode)
 
 
-@pytest.mark.parametrize("mode", [0, 1, 2])
+@pytest.mark.parametrize("mode", [0, 1, 2, 3])
 def test_matvec_full_size_eigenvector(g, mode):
     # d=10, n=64 (the convection-diffusion workload's operator): A q = lambda q
     # exactly for a rank-1 tensor of eigenvectors; sampled entries are checked.

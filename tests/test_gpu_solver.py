@@ -84,7 +84,8 @@ def test_convdiff_full_size_solution_error(g):
     # sum_k I x L x I (B is skew), so x^T A x >= d lambda_1(L) ||x||^2 and
     # sigma_min(A) >= d lambda_1(L): two solutions with residuals r1, r2 differ
     # by at most (r1 + r2) / (d lambda_1(L)).  Each mode's solution at tol 1e-6
-    # must meet that bound and the targets 1e-5 (FP64) and 1e-4 (float modes).
+    # must meet that bound and the targets 1e-5 (FP64) and 1e-4 (FP32, split
+    # TF32 and split BF16).
     # The targets need the tighter sketched stop (stop_safety 0.01): the
     # residual alone bounds the error only through that factor, and at the
     # default 0.1 the FP64 solve's error measured 1.9e-5.
@@ -98,7 +99,7 @@ def test_convdiff_full_size_solution_error(g):
     lam1 = cf.laplacian_eig(n)[0][0]
     xrn = ott.norm(xr)
     errs = {}
-    for mode, target in ((0, 1e-5), (1, 1e-4), (2, 1e-4)):
+    for mode, target in ((0, 1e-5), (1, 1e-4), (2, 1e-4), (3, 1e-4)):
         x, info = solve(g, w, mode, stop_safety=0.01)
         assert info["status"] == 0
         xm = x.numpy()
@@ -108,3 +109,14 @@ def test_convdiff_full_size_solution_error(g):
         assert err <= (r + rr) / (d * lam1 * xrn), (mode, err)
         errs[mode] = (err, target)
     assert all(e <= t for e, t in errs.values()), errs
+
+
+def test_convdiff_full_size_bf16(g):
+    # split-BF16 tensor-core matvec (about 2^-17 per product), FP32 elsewhere,
+    # FP64 QR / least squares / residual; refinement restarts until the true
+    # residual is met
+    w = ti.workload("convdiff")
+    x, info = solve(g, w, g.MODE_BF16)
+    assert info["status"] == 0
+    res = osol.true_residual_norm(w.op, x.numpy(), w.b) / ott.norm(w.b)
+    assert res <= 1e-6
