@@ -309,8 +309,9 @@ def extra_configs(torch, g, flush, stream, modes):
     Laplacian (d = 4, n = 16), the headline system in split-BF16 mode, the
     large-rank Laplacian (d = 20, n = 128, rank
     cap 128) in the mixed mode and in FP64, the preconditioned Markov-chain
-    system (d = 5, n = 128) in FP64 and FP32, and one forward + adjoint
-    solve of the differentiable workload (d = 12, n = 64)."""
+    system (d = 5, n = 128) in FP64 and FP32, the 64-right-hand-side batch
+    (d = 8, n = 32) through the worker pool, and one forward + adjoint solve
+    of the differentiable workload (d = 12, n = 64)."""
     out = {}
 
     def solve_cfg(name, mode, reps):
@@ -357,7 +358,7 @@ def extra_configs(torch, g, flush, stream, modes):
         blocks, a, bnd = ti.markov_precond_blocks(w.extra["Q"], shift_frac=frac)
         P = g.Precond.for_interval(a, bnd, 1e-2, [torch.as_tensor(B, device="cuda") for B in blocks])
         kw = dict(maxit=p["maxit"], tol=p["tol"], rmax=80, mode=mval, s=p["s"], eta=p["eta"],
-                  r_sol=80, oversample=p["oversample"], seed=0, max_restarts=10)
+                  r_sol=80, oversample=p["oversample"], seed=0, max_restarts=20)
         g.tt_spgmres_solve(op, P, b, **kw)  # warm
         ts = []
         for _ in range(2):
@@ -375,6 +376,32 @@ def extra_configs(torch, g, flush, stream, modes):
                      "max_rank": inf["max_rank"], "precond_terms": len(P.alpha),
                      "shift_of_gap": frac}
     out["markov_d5_n128_preconditioned_rank80"] = mk
+    # the batched workload: all 64 right-hand sides (d = 8, n = 32 Laplacian,
+    # bond ranks U{1..12}, rank cap 150) through the library's worker pool,
+    # FP32 contractions (with the split-TF32 matvec the hardest right-hand
+    # side levels off near the 1e-6 target at this rank cap), one timed batch
+    # after a warm call on two right-hand sides
+    w = ti.workload("batched")
+    p = w.params
+    op = g.op_to_device(w.op)
+    bs = [g.TT.from_numpy(b) for b in w.b]
+    kw = dict(maxit=p["maxit"], tol=p["tol"], rmax=p["rmax"], mode=g.MODE_FP32, s=p["s"],
+              round_tol=p["round_tol"], r_sol=p["r_sol"], oversample=p["oversample"],
+              max_restarts=20, nworkers=16)
+    g.tt_sgmres_solve_batched(op, bs[:2], **kw)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    res = g.tt_sgmres_solve_batched(op, bs, **kw)
+    torch.cuda.synchronize()
+    sec = time.perf_counter() - t0
+    out["batched_d8_n32_64rhs"] = {"fp32": {
+        "seconds": sec, "rhs_per_s": len(bs) / sec, "workers": 16,
+        "not_converged": int(sum(i["status"] != 0 for _, i in res)),
+        "max_true_res": max(i["true_res"] for _, i in res),
+        "iters_mean": float(np.mean([i["iters"] for _, i in res])),
+        "iters_max": int(max(i["iters"] for _, i in res))}}
+    del res, bs, op
+    torch.cuda.empty_cache()
     # differentiable workload: forward solve + adjoint solve + backward contractions
     w = ti.workload("differentiable")
     p = w.params
@@ -626,10 +653,11 @@ def run_round_case(args):
 def run_batched_case(args):
     """The batched workload: 64 right-hand sides (d=8, n=32 Laplacian, bond
     ranks U{1..12}, rank cap 150), solved by the library's worker pool in the
-    selected mode; one JSON line with the whole-batch time and RHS/s."""
+    selected mode (default FP32); one JSON line with the whole-batch time and
+    RHS/s."""
     import torch
     import paper_2409_09471_gb300 as g
-    mode_name = args.mode or "tf32"
+    mode_name = args.mode or "fp32"
     mode = {"tf32": g.MODE_TF32, "fp32": g.MODE_FP32, "fp64": g.MODE_FP64}[mode_name]
     w = ti.workload("batched")
     p = w.params
@@ -637,7 +665,7 @@ def run_batched_case(args):
     bs = [g.TT.from_numpy(b) for b in w.b]
     kw = dict(maxit=p["maxit"], tol=p["tol"], rmax=p["rmax"], mode=mode, s=p["s"],
               round_tol=p["round_tol"], r_sol=p["r_sol"], oversample=p["oversample"],
-              max_restarts=10, nworkers=args.workers)
+              max_restarts=40, nworkers=args.workers)
     times = []
     for i in range(args.warmup + args.steps):
         torch.cuda.synchronize()

