@@ -145,7 +145,11 @@ struct TcCoreArgs {
 void matvec_tc_cores(const std::vector<TcCoreArgs>& cores, int* err, cudaStream_t st,
                      bool bf16 = false);
 // Device scratch for split-K partial sums (set per API call; null disables split-K).
+// GEMMs enqueued on another stream of the same call switch to a scratch of
+// their own around their launches (the pointer is read at launch time).
 void set_gemm_scratch(void* ws, size_t bytes);
+void* gemm_split_ws();
+size_t gemm_split_bytes();
 constexpr size_t GEMM_SCRATCH_BYTES = size_t(48) << 20;
 
 // Row-major plain helper: C (MxN, ldc) = alpha * A (MxK, lda) * B (KxN, ldb) + beta*C

@@ -268,6 +268,8 @@ void set_gemm_scratch(void* ws, size_t bytes) {
   g_split_ws = ws;
   g_split_bytes = ws ? bytes : 0;
 }
+void* gemm_split_ws() { return g_split_ws; }
+size_t gemm_split_bytes() { return g_split_bytes; }
 
 void gemm_fp32_simt(const std::vector<GemmProblem>& probs, cudaStream_t st) {
   if (g_dry_run) return;

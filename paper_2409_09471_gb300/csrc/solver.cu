@@ -6,9 +6,12 @@
 //
 // Per iteration (all on the device; the host reads the new ranks and the
 // sketched residual once):
-//   w = A v_k (untruncated)  ->  W[:, k] = S w  ->  h = <w, v_k>
-//   v~ = Round(w - h v_k, round_tol, rmax)  ->  v_{k+1} = v~ / ||v~||
-//   y = argmin ||W y - S r0||, stop when ||W y - S r0|| <= inner_tol ||S r0||.
+//   w = A v_k (untruncated)
+//   second stream: h = <w, v_k>, then W[:, k] = S w
+//   v~ = Round(w - h v_k, round_tol, rmax) (its left sweep waits for h)
+//     ->  v_{k+1} = v~ / ||v~||
+//   y = argmin ||W y - S r0|| (after W[:, k]), stop when
+//   ||W y - S r0|| <= inner_tol ||S r0||.
 #include "solver.cuh"
 #include <type_traits>
 #include <chrono>
@@ -43,6 +46,26 @@ double inner_floor(int mode) {
     default: return 1e-6;
   }
 }
+
+// Second stream of one solve, with the events that order it against the
+// solver's own stream; released when the solve returns (pending work is not
+// waited for by cudaStreamDestroy, it completes first).
+struct SideStream {
+  cudaStream_t st = nullptr;
+  cudaEvent_t fork = nullptr, dots = nullptr, sketch = nullptr;
+  void create() {
+    TT_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+    TT_CUDA(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
+    TT_CUDA(cudaEventCreateWithFlags(&dots, cudaEventDisableTiming));
+    TT_CUDA(cudaEventCreateWithFlags(&sketch, cudaEventDisableTiming));
+  }
+  ~SideStream() {
+    if (fork) cudaEventDestroy(fork);
+    if (dots) cudaEventDestroy(dots);
+    if (sketch) cudaEventDestroy(sketch);
+    if (st) cudaStreamDestroy(st);
+  }
+};
 
 template <typename T>
 TTv<T> alloc_tt(Arena& ar, int d, const int64_t* n, const int64_t* cap) {
@@ -304,6 +327,33 @@ SolveResult sgmres_solve(const Ctx& c0, const TTop<double>& A64in, const TTv<dou
     e2 = alloc_tt<T>(ar, d, n, xcap.data());
   }
 
+  // ---- side stream: an iteration's inner products <w, v_i> and its sketch
+  // S w run on a second stream, concurrently with the rounding's
+  // right-to-left partial contractions and its left-to-right QR sweep (FP64
+  // latency-bound work that leaves most of the GPU idle).  They take their
+  // temporaries from a slice of their own and their split-K sums from a
+  // scratch of their own; events order them before the rounding's left sweep
+  // (the coefficients) and before the least squares (the sketch column).
+  int64_t wmax = 1, vmax = 1, nmax = 1;
+  for (int k = 0; k <= d; ++k) {
+    wmax = std::max(wmax, wcap[k]);
+    vmax = std::max(vmax, vcap[k]);
+  }
+  for (int k = 0; k < d; ++k) nmax = std::max(nmax, n[k]);
+  const size_t side_bytes =
+      sizeof(T) * (size_t)(2 * s * wmax + wmax * nmax * vmax + 2 * wmax * vmax) + 8 * 256;
+  Arena ar_side(ar.take<char>((int64_t)side_bytes), side_bytes, g_dry_run);
+  void* side_split = ar.take<char>((int64_t)GEMM_SCRATCH_BYTES);
+  // Not used when independent solves already share the GPU (the batched
+  // worker pool): there the other solves fill it, and the extra streams only
+  // add scheduling work.
+  const bool use_side = !g_dry_run && !g_qr_narrow;
+  SideStream side;
+  if (use_side) side.create();
+  Ctx cs = c;
+  cs.ar = &ar_side;
+  if (use_side) cs.st = side.st;
+
   if (g_dry_run) {
     // workspace query: run every scratch-using step once at capacity ranks
     for (auto& v : V) for (int q = 0; q <= d; ++q) v.r[q] = vcap[q];
@@ -372,22 +422,35 @@ SolveResult sgmres_solve(const Ctx& c0, const TTop<double>& A64in, const TTv<dou
       }
       for (int q = 0; q <= d; ++q) w.r[q] = A64.R[q] * av->r[q];
       tt_matvec_dev<T>(c, A, *av, w);
-      // W[:, k] = S w
-      tt_sketch_dev<T>(c, w, s, (const T* const*)S.data(), Wm + k * s);
-      // h_{i,k} = <w, v_i> for the last ell basis vectors (Sec. 3.4), then
-      // v~ = Round(w - sum_i h_{i,k} v_i)
+      // side stream: h_{i,k} = <w, v_i> for the last ell basis vectors
+      // (Sec. 3.4), then W[:, k] = S w
+      if (use_side) {
+        TT_CUDA(cudaEventRecord(side.fork, c.st));
+        TT_CUDA(cudaStreamWaitEvent(side.st, side.fork, 0));
+      }
+      void* const main_split = gemm_split_ws();
+      const size_t main_split_bytes = gemm_split_bytes();
+      set_gemm_scratch(side_split, GEMM_SCRATCH_BYTES);
       const int first = std::max(0, k - ell + 1);
       std::vector<Term<T>> terms(1 + (k - first + 1));
       terms[0].X = w;
       for (int i = first; i <= k; ++i) {
         double* hi = i == k ? scal + 1 : hcoef + i;
-        tt_dot_dev<T>(c, w, VS(i), hi);
+        tt_dot_dev<T>(cs, w, VS(i), hi);
         Term<T>& t = terms[1 + i - first];
         t.X = VS(i);
         t.coef = -1.0;
         t.coef_dev = hi;
       }
-      tt_round_rand_dev<T>(c, terms, round_tol, p.rmax, p.oversample, drm, VS(k + 1));
+      if (use_side) TT_CUDA(cudaEventRecord(side.dots, side.st));
+      tt_sketch_dev<T>(cs, w, s, (const T* const*)S.data(), Wm + k * s);
+      if (use_side) TT_CUDA(cudaEventRecord(side.sketch, side.st));
+      set_gemm_scratch(main_split, main_split_bytes);
+      // v~ = Round(w - sum_i h_{i,k} v_i): its partial contractions start at
+      // once, its left sweep waits for the coefficients
+      Ctx cr = c;
+      cr.left_wait = use_side ? side.dots : nullptr;
+      tt_round_rand_dev<T>(cr, terms, round_tol, p.rmax, p.oversample, drm, VS(k + 1));
       // h_{k+1,k} = ||v~||: the norm of core 1 when cores 2..d are
       // right-orthogonal (FP64 mode), otherwise the Gram sweep
       if (f64) sumsq(VS(k + 1).core[0], f64, VS(k + 1).core_elems(0), scal + 2, c.scratch + 16, c.st);
@@ -399,6 +462,7 @@ SolveResult sgmres_solve(const Ctx& c0, const TTop<double>& A64in, const TTv<dou
         sg.sa = 1; sg.src_f64 = f64; sg.dst_f64 = f64; sg.scale_dev = scal + 3; sg.scale_dev_inv = 1;
         copy3d({sg}, c.st);
       }
+      if (use_side) TT_CUDA(cudaStreamWaitEvent(c.st, side.sketch, 0));
       lstsq_add_column(Wm, Sr0, s, k, p.maxit, lsws, ydev, scal + 4, c.st);
       // scal[1..4]: h_{k,k}, ||v~||^2, ||v~|| = h_{k+1,k}, sketched residual
       double hs4[4] = {0.0, 1.0, 1.0, 1.0};

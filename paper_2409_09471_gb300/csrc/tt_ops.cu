@@ -267,6 +267,7 @@ void tt_round_rand_dev(const Ctx& c, const std::vector<Term<T>>& terms, double e
   }
 
   // 3. left sweep: Z = M x_1 X, Y = Z W, Y = Q R, core <- Q, M = Q^T Z
+  if (c.left_wait && !g_dry_run) TT_CUDA(cudaStreamWaitEvent(c.st, c.left_wait, 0));
   int64_t zmax = 1, mmax = 1, ymax = 1;
   for (int mu = 1; mu < d; ++mu) {
     zmax = std::max(zmax, ell[mu - 1] * n[mu - 1] * Ts[mu]);

@@ -13,6 +13,10 @@ struct Ctx {
   int* err = nullptr;        // device flags: err[0] bit 0 = QR barrier timeout,
                              // err[1] = Jacobi sweep-cap count
   double* scratch = nullptr; // device scratch for reductions (>= 256 doubles)
+  // randomized rounding only: an event the left-to-right sweep waits for (the
+  // term coefficients on the device are read from that sweep on; the
+  // right-to-left partial contractions before it do not need them)
+  cudaEvent_t left_wait = nullptr;
   bool f64() const { return mode == TT_MODE_FP64; }
 };
 
