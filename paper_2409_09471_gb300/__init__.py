@@ -541,6 +541,12 @@ class _SolveLoss(torch.autograd.Function):
     """``loss(theta, b) = ||x - x_t||^2`` with ``A(theta) x = b`` and
     ``A(theta) = sum_k theta_k (I x .. x M x .. x I)``.
 
+    The difference ``x - x_t`` is formed as a TT by the FP64 randomized rounding
+    at full rank (sum of the two rank caps, tolerance far below the solver's),
+    which leaves it left-orthogonal, so the loss is its squared norm without
+    the cancellation of ``<x, x> - 2 <x, x_t> + <x_t, x_t>`` when x is close to
+    x_t.
+
     Backward: ``lambda = A^{-T} 2 (x - x_t)`` by a second TT-sGMRES solve on the
     transposed operator, then ``dL/dtheta_k = -<lambda, (I x .. M .. x I) x>``
     (tt_local_dots), ``dL/db_k = d<lambda, b>/db_k`` and ``dL/dxt_k =
@@ -553,11 +559,15 @@ class _SolveLoss(torch.autograd.Function):
         xt = TT(cores[d:])
         mats = [M] * d
         op = tt_kron_sum_op(mats, theta)
-        x, info = tt_sgmres_solve(op, b, **cfg["solver"])
-        loss = (tt_dot(x, x) - 2.0 * tt_dot(x, xt) + tt_dot(xt, xt)).reshape(())
+        sv = cfg["solver"]
+        x, info = tt_sgmres_solve(op, b, **sv)
+        rmax_r = max(x.ranks) + max(xt.ranks)
+        diff = tt_round_rand([x, xt], [1.0, -1.0], 1e-12, rmax_r,
+                             oversample=sv.get("oversample", 10), seed=sv.get("seed", 0) + 1)
+        loss = tt_dot(diff, diff).reshape(())
         ctx.cfg = cfg
         ctx.info = info
-        ctx.save_for_backward(theta, M, *x.cores, *cores)
+        ctx.save_for_backward(theta, M, *x.cores, *cores, *diff.cores)
         ctx.xd = x.d
         cfg["last_info"] = info
         return loss
@@ -571,12 +581,11 @@ class _SolveLoss(torch.autograd.Function):
         x = TT(saved[2:2 + d])
         b = TT(saved[2 + d:2 + 2 * d])
         xt = TT(saved[2 + 2 * d:2 + 3 * d])
+        diff = saved[2 + 3 * d:2 + 4 * d]
         sv = cfg["solver"]
-        # right-hand side of the adjoint system: 2 (x - x_t), rounded in FP64
-        # far below the solver tolerance
-        rmax_r = max(x.ranks) + max(xt.ranks)
-        r = tt_round_rand([x, xt], [2.0, -2.0], 1e-12, rmax_r, oversample=sv.get("oversample", 10),
-                          seed=sv.get("seed", 0) + 1)
+        # right-hand side of the adjoint system: 2 (x - x_t), the forward's
+        # FP64 rounding of the difference scaled by 2
+        r = TT([2.0 * diff[0], *diff[1:]])
         opT = tt_op_transpose(tt_kron_sum_op([M] * d, theta))
         lam, info = tt_sgmres_solve(opT, r, **sv)
         cfg["last_adjoint_info"] = info

@@ -112,6 +112,28 @@ def test_solve_loss_gradients_vs_dense_oracle(g):
     assert np.isclose(xc[k].grad[idx].item(), fd, rtol=1e-5, atol=1e-9)
 
 
+def test_solve_loss_at_the_solution_does_not_cancel(g):
+    # x_t = the exact solution (dense solve, compressed by the oracle's TT-SVD):
+    # the loss is ||x - x*||^2 for the FP64 solve at tol 1e-12 (relative error
+    # <= kappa 1e-12, kappa ~ 32 here), far below the ~1e-16 ||x*||^2 that
+    # <x,x> - 2 <x,x*> + <x*,x*> would leave, with either sign, after cancelling
+    from oracle import closed_forms as cf, rounding as ornd
+    d, n = 3, 8
+    theta = np.array([0.7, 1.3, 1.9])
+    L = ti.laplacian_1d(n)
+    b = ti.random_tt([n] * d, [1, 3, 2, 1], seed=30)
+    xs = cf.kron_sum_solve_dense([t * L for t in theta], ott.full(b))
+    cores = [np.eye(n).reshape(1, n, n), np.eye(n * n).reshape(n, n, n * n),
+             xs.reshape(n * n, n, 1)]
+    xt = ornd.tt_svd_round(cores, 0.0)
+    assert np.allclose(ott.full(xt), xs, rtol=0, atol=1e-13 * np.abs(xs).max())
+    th = torch.tensor(theta, dtype=torch.float64)
+    bc = [torch.as_tensor(c, device="cuda") for c in b]
+    xc = [torch.as_tensor(c, device="cuda") for c in xt]
+    loss = g.solve_loss(th, torch.as_tensor(L, device="cuda"), bc, xc, **SOLVE64).item()
+    assert 0.0 <= loss <= 1e-18 * float(np.sum(xs ** 2)), loss
+
+
 def test_solve_loss_gradients_vs_finite_differences(g):
     # d=5, n=16: central differences of the library's own FP64 solves.  The
     # solutions are capped at rank 60, which floors the true residual near 5e-8
