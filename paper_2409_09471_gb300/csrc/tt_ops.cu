@@ -422,12 +422,18 @@ void tt_round_rand_dev(const Ctx& c, const std::vector<Term<T>>& terms, double e
       ja.vtmp[b - 1] = Gd[b];  // the FP64 Gram is consumed by the Cholesky factorisation
     }
     jacobi_svd_batched(ja, c.st);
+    // one host read for the ranks and the error word (only the QRs and the
+    // tensor-core kernels set error bits, and they have all run by now)
     std::vector<int> rh(d + 1, 1);
+    int flags = 0;
     if (!g_dry_run) {
       TT_CUDA(cudaMemcpyAsync(rh.data() + 1, rks + 1, sizeof(int) * (d - 1), cudaMemcpyDeviceToHost,
                               c.st));
+      TT_CUDA(cudaMemcpyAsync(&flags, c.err, sizeof(int), cudaMemcpyDeviceToHost, c.st));
       TT_CUDA(cudaStreamSynchronize(c.st));
     }
+    if (flags & 1) throw Error(TT_ERR_TIMEOUT, "a grid barrier of the FP64 QR timed out");
+    if (flags & 4) throw Error(TT_ERR_TIMEOUT, "an mbarrier wait of a tensor-core kernel timed out");
     rh[0] = rh[d] = 1;
     // W_b = V_b[:, :r_b] in the working precision
     // (buffers sized by the rank caps min(l_b, rmax), so that the workspace
@@ -465,7 +471,6 @@ void tt_round_rand_dev(const Ctx& c, const std::vector<Term<T>>& terms, double e
     gemm(c.mode, p1, c.st);
     gemm(c.mode, p2, c.st);
     for (int k = 0; k <= d; ++k) y.r[k] = rh[k];
-    check_device_flags(c);
     ar.release(mk);
     return;
   }
