@@ -355,6 +355,11 @@ typedef struct {
  * and the loop restarts from it until ||b - A x|| <= tol ||b||.
  * A and b are given in FP64 (double cores, device); x (device, double cores,
  * capacities >= r_sol) receives the solution.  Synchronises.
+ * Each iteration's inner products <A v_k, v_i> and sketch S A v_k run on a
+ * second CUDA stream that the call creates (with three events) and releases
+ * before it returns; ``stream`` waits on it where their results are used, so
+ * the call is ordered on ``stream`` as a whole.  (Inside
+ * tt_sgmres_solve_batched every solve stays on its worker's stream.)
  */
 int tt_sgmres_solve(const tt_op* A, const tt_vec* b, const tt_solver_params* p,
                     const tt_vec_out* x, tt_solver_info* info, void* ws, size_t ws_bytes,
