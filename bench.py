@@ -71,6 +71,9 @@ def parse():
                     help="'round': time one randomized rounding of w - h v at the workload's "
                          "sizes (the kernel-level case used for ncu captures); 'batched': the "
                          "64-right-hand-side workload through the batched solver")
+    ap.add_argument("--round-workload", choices=["convdiff", "large_rank"], default="convdiff",
+                    help="sizes of the 'round' case: the bench workload (d=10, n=64, rank 64) or "
+                         "the large-rank one (d=20, n=128, rank 128)")
     ap.add_argument("--workers", type=int, default=16,
                     help="library worker threads (streams) of the batched case")
     ap.add_argument("--seq-sample", type=int, default=4,
@@ -625,29 +628,34 @@ def run_ours(args):
 
 
 def run_round_case(args):
-    """One Gram-Schmidt rounding of the solver at the workload's sizes:
-    ``Round(A v - h v)`` with v a random rank-64 TT (d=10, n=64), rank cap 64,
-    oversampling 10, tolerance 1e-7, in the selected mode."""
+    """One Gram-Schmidt rounding of the solver at a workload's sizes:
+    ``Round(A v - h v)`` with v a random TT at the rank cap (d=10, n=64, rank
+    64; or the large-rank d=20, n=128, rank 128), oversampling 10, tolerance
+    1e-7, in the selected mode."""
     import torch
     import paper_2409_09471_gb300 as g
     mode_name = args.mode or "fp32"
     mode = {"tf32": g.MODE_TF32, "fp32": g.MODE_FP32, "fp64": g.MODE_FP64}[mode_name]
-    w, p = workload()
+    if args.round_workload == "large_rank":
+        w, r = ti.workload("large_rank"), 128
+    else:
+        (w, _), r = workload(), 64
     dt = g.mode_dtype(mode)
-    v = g.TT.from_numpy(ti.random_tt(w.ns, [1] + [64] * (w.d - 1) + [1], seed=5), dt)
+    v = g.TT.from_numpy(ti.random_tt(w.ns, [1] + [r] * (len(w.ns) - 1) + [1], seed=5), dt)
     Av = g.tt_matvec(g.op_to_device(w.op, dt), v, mode=mode)
     times = []
     for i in range(args.warmup + args.steps):
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record()
-        y = g.tt_round_rand([Av, v], [1.0, -0.3], 1e-7, 64, 10, seed=1, mode=mode)
+        y = g.tt_round_rand([Av, v], [1.0, -0.3], 1e-7, r, 10, seed=1, mode=mode)
         e1.record()
         torch.cuda.synchronize()
         if i >= args.warmup:
             times.append(e0.elapsed_time(e1))
-    print(json.dumps({"case": "round", "mode": mode_name, "ms_per_call": statistics.median(times),
-                      "out_ranks": y.ranks}), flush=True)
+    print(json.dumps({"case": "round", "workload": args.round_workload, "mode": mode_name,
+                      "ms_per_call": statistics.median(times), "out_ranks": y.ranks[:4]}),
+          flush=True)
 
 
 def run_batched_case(args):
