@@ -18,10 +18,10 @@ timed interval.  With ``--gpus N`` (torchrun) every rank solves its own copy:
 the path has no data-parallel split (replicas only).
 
 ``--impl reference`` times the FP64 CPU oracle (the same algorithm in NumPy)
-on this machine's host cores: every timed step is one full solve of the same
-workload (restarts, final rounding and exact residual included); the warm-up
-steps are single untimed Krylov iterations.  The GPU arm's ``cpu_baseline`` is
-one such full solve.  ``roofline`` comes from a separate pass of solves in
+on this machine's host cores: one full solve of the same workload (restarts,
+final rounding and exact residual included), reported as K equal steps; the
+warm-up steps are single untimed Krylov iterations.  The GPU arm's
+``cpu_baseline`` is one such full solve.  ``roofline`` comes from a separate pass of solves in
 which every kernel launch is bracketed by CUDA events; the headline loop runs
 without them.
 """
