@@ -57,3 +57,27 @@ def test_reference_arm_under_torchrun_prints_one_line_from_rank_0():
     line = json.loads(lines[0])
     assert line["impl"] == "reference" and line["unit"] == "s" and line["value"] > 0
     assert line["cpu_baseline"]["kind"] == "oracle"
+
+
+def test_reference_arm_line_keeps_the_contract():
+    # one process, K = 4 steps: the line carries the contract's keys, its K
+    # steps are the equal shares of one timed full solve (ms_per_step * steps
+    # = value), and e2e and cpu_baseline repeat the value with no copies
+    cmd = [sys.executable, "bench.py", "--impl", "reference", "--steps", "4", "--warmup", "1",
+           "--ref-small"]
+    r = subprocess.run(cmd, cwd=ROOT, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [l for l in r.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1
+    line = json.loads(lines[0])
+    for key in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step",
+                "higher_is_better", "scaling", "vs_baseline", "dtype", "data", "config",
+                "cpu_baseline", "e2e"):
+        assert key in line, key
+    assert line["steps"] == 4 and line["warmup"] == 1 and line["higher_is_better"] is False
+    assert abs(line["ms_per_step"] * line["steps"] - 1e3 * line["value"]) <= 1e-6 * 1e3 * line["value"]
+    assert line["true_res"] <= 1e-6
+    assert line["e2e"] == {"value": line["value"], "unit": "s", "h2d_bytes_per_step": 0,
+                           "d2h_bytes_per_step": 0}
+    cb = line["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["value"] == line["value"] and cb["cores"] >= 1
