@@ -106,6 +106,41 @@ def test_rto_scale_of_drm_irrelevant():
     assert np.allclose(tt.full(a), tt.full(b), atol=1e-13)
 
 
+@pytest.mark.parametrize("eps", [1e-1, 1e-3])
+def test_rto_equals_tt_svd_when_the_sketch_rank_covers_the_tensor(eps):
+    # sketch ranks l >= the sum's representation ranks: the randomized range
+    # finder reproduces the sum exactly (the DRM contractions have full column
+    # rank with probability one); with no singular value below the threshold
+    # the truncation keeps it, and the result is the oracle's TT-SVD rounding
+    # of the same tensor: same ranks, same tensor to rounding
+    ns = [4, 5, 4, 3]
+    z = [(0.7 - 0.3 * s, ti.random_tt(ns, [1, 3, 4, 2, 1], seed=20 + s)) for s in range(3)]
+    drm = ti.gaussian_drm(ns, [1, 70, 70, 70, 1], seed=30)
+    y = rnd.rto_round(z, drm, eps=eps, rmax=60, oversample=10)
+    ref = rnd.tt_svd_round(tt.add(z), eps=eps, rmax=60)
+    assert tt.ranks(y) == tt.ranks(ref)
+    yf, rf = tt.full(y), tt.full(ref)
+    assert np.linalg.norm(yf - rf) <= 1e-10 * np.linalg.norm(rf)
+
+
+def test_rto_truncation_matches_tt_svd_across_a_spectral_gap():
+    # T = X + delta Y with X of TT rank (3, 4, 2) and ||delta Y|| = 1e-8 ||X||,
+    # rounded at eps = 1e-4: both truncation sweeps (right-to-left after the
+    # randomized left sweep, and the oracle's left-to-right TT-SVD) drop exactly
+    # the tail, so they keep X's ranks and agree to the size of the tail
+    ns = [4, 5, 4, 3]
+    X = ti.random_tt(ns, [1, 3, 4, 2, 1], seed=40)
+    Y = ti.random_tt(ns, [1, 2, 3, 2, 1], seed=41)
+    delta = 1e-8 * tt.norm(X) / tt.norm(Y)
+    z = [(1.0, X), (delta, Y)]
+    drm = ti.gaussian_drm(ns, [1, 70, 70, 70, 1], seed=42)
+    y = rnd.rto_round(z, drm, eps=1e-4, rmax=60, oversample=10)
+    ref = rnd.tt_svd_round(tt.add(z), eps=1e-4, rmax=60)
+    assert tt.ranks(y) == tt.ranks(ref) == [1, 3, 4, 2, 1]
+    yf, rf = tt.full(y), tt.full(ref)
+    assert np.linalg.norm(yf - rf) <= 1e-7 * np.linalg.norm(rf)
+
+
 def test_rto_vs_tt_svd_heuristic():
     # parity unpinned beyond this heuristic: randomized error within 10x of
     # the deterministic truncation error at equal rank, over 20 seeds
