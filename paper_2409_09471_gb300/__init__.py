@@ -79,6 +79,9 @@ class TT:
 
 
 def op_to_device(op, dtype=torch.float64, device="cuda"):
+    """TT operator cores (``[R_{k-1}, n_out, n_in, R_k]`` arrays or tensors) as
+    contiguous device tensors of ``dtype`` (float64 for the solvers, the mode's
+    dtype for :func:`tt_matvec`)."""
     return [torch.as_tensor(c, dtype=dtype, device=device).contiguous() for c in op]
 
 
